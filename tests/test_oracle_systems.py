@@ -1,0 +1,304 @@
+"""Pins of the oracle's model equations and solvers (CPU only).
+
+Each test checks the oracle against something other than itself: closed-form
+solutions, invariant sets, equilibria, an independently derived dimensional
+form of the Keller-Miksis equation, its linearisation integrated by SciPy, the
+bouncing-ball closed form for the event machinery, and numbers printed in the
+paper (tests/golden/).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+WATER_CFG = dict(rho=997.0, c=1497.0, mu=8.9e-4, sigma=0.0725, pv=3166.8, pinf=1.0e5, gamma=1.4)
+
+
+def _liq(d):
+    return oracle.liquid(d["rho"], d["c"], d["mu"], d["sigma"], d["pv"], d["pinf"], d["gamma"])
+
+
+# ---------------------------------------------------------------------------
+# x' = x^2 - p (Sec. 3)
+# ---------------------------------------------------------------------------
+
+def _x2p_exact(p, x0, t):
+    s = math.sqrt(p)
+    if abs(x0) < s:          # x = -s tanh(s (t + C))
+        return -s * math.tanh(s * t + math.atanh(-x0 / s))
+    # |x0| > s with x0 < 0: x = -s coth(s (t + C))
+    u = s * t + math.atanh(s / -x0)
+    return -s / math.tanh(u)
+
+
+@pytest.mark.parametrize("p", [0.1, 0.2, 0.37, 1.0])
+def test_x2p_matches_closed_form(p):
+    y, st = oracle.rk4_solve(oracle.X2P, [[p]], [[-0.5]], 0.0, 0.01, 1000)
+    exact = _x2p_exact(p, -0.5, 10.0)
+    assert abs(y[0, 0] - exact) < 1e-9 * abs(exact)
+    y2, _ = oracle.rk4_solve(oracle.X2P, [[p]], [[-0.5]], 0.0, 0.02, 500)
+    # fourth order: doubling h multiplies the error by ~16
+    e1, e2 = abs(y[0, 0] - exact), abs(y2[0, 0] - exact)
+    if e1 > 1e-13:           # above rounding level
+        assert 10.0 < e2 / e1 < 22.0
+
+
+# ---------------------------------------------------------------------------
+# Lorenz (Sec. 4.1)
+# ---------------------------------------------------------------------------
+
+LOR = dict(sigma=10.0, b=8.0 / 3.0)
+
+
+def _lor_params(rho):
+    rho = np.atleast_1d(np.asarray(rho, dtype=float))
+    return np.stack([rho, np.full_like(rho, LOR["sigma"]), np.full_like(rho, LOR["b"])])
+
+
+def test_lorenz_invariant_axis_decays_exponentially():
+    """x = y = 0 is invariant and there z' = -b z: RK4 multiplies z by the
+    Taylor polynomial R(-b h) each step, and R^N tends to exp(-b t) at order 4."""
+    y, _ = oracle.rk4_solve(oracle.LORENZ, _lor_params(15.0), [[0.0], [0.0], [10.0]], 0.0, 0.01, 1000)
+    exact = 10.0 * math.exp(-LOR["b"] * 10.0)
+    z = -LOR["b"] * 0.01
+    rk = 10.0 * (1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24) ** 1000
+    assert y[0, 0] == 0.0 and y[1, 0] == 0.0
+    assert abs(y[2, 0] / rk - 1.0) < 1e-12
+    assert abs(y[2, 0] / exact - 1.0) < 5e-7
+    y2, _ = oracle.rk4_solve(oracle.LORENZ, _lor_params(15.0), [[0.0], [0.0], [10.0]], 0.0, 0.02, 500)
+    assert 12.0 < abs(y2[2, 0] / exact - 1.0) / abs(y[2, 0] / exact - 1.0) < 20.0
+
+
+@pytest.mark.parametrize("rho", [2.0, 7.5, 13.0, 19.0])
+def test_lorenz_rhs_vanishes_at_nontrivial_equilibria(rho):
+    s = math.sqrt(LOR["b"] * (rho - 1.0))
+    for sign in (1.0, -1.0):
+        yy = np.array([[sign * s], [sign * s], [rho - 1.0]])
+        dy = oracle.rhs(oracle.LORENZ, _lor_params(rho), 0.0, yy)
+        assert np.abs(dy).max() < 1e-13 * max(1.0, rho)
+
+
+def test_lorenz_long_runs_converge_to_attractors():
+    """rho < 1: origin; 1 < rho < 13.9 (no transient chaos): C+ or C-."""
+    rho = np.array([0.3, 0.8, 2.0, 5.0, 9.0, 12.0])
+    n = rho.size
+    y, st = oracle.rk4_solve(oracle.LORENZ, _lor_params(rho), np.full((3, n), 10.0), 0.0, 0.01, 50000)
+    assert np.all(st == 0)
+    for i, r in enumerate(rho):
+        if r < 1.0:
+            assert np.abs(y[:, i]).max() < 1e-8
+        else:
+            s = math.sqrt(LOR["b"] * (r - 1.0))
+            target = np.array([math.copysign(s, y[0, i]), math.copysign(s, y[0, i]), r - 1.0])
+            assert np.abs(y[:, i] - target).max() < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# Keller-Miksis (Sec. 4.2)
+# ---------------------------------------------------------------------------
+
+def test_km_equilibrium_without_driving():
+    """P_A = 0: N_KM(1, 0) = C0 - C2 - C3 = 0, so y = (1, 0) is a fixed point.
+    The explicit solver runs at the largest step its error test allows, so the
+    state wanders off the fixed point only at the tolerance level."""
+    liq = _liq(WATER_CFG)
+    f = np.array([2e4, 1e5, 1e6])
+    C = oracle.km_coefficients(0.0, f, 0.0, 0.0, 0.0, 10e-6, liq)
+    assert np.all(C[5:9] == 0.0)
+    dy = oracle.rhs(oracle.KM, C, 0.3, np.stack([np.ones(3), np.zeros(3)]))
+    assert np.all(np.abs(dy[1]) <= 1e-14 * C[0])
+    tol = oracle.make_tol(rtol=1e-10, atol=1e-10, dt0=1e-2, dt_min=1e-14, dt_max=1e-1,
+                          n_phases=64, phase_len=1.0, t0=0.0)
+    r = oracle.cashkarp_solve(oracle.KM, C, np.stack([np.ones(3), np.zeros(3)]), tol)
+    assert np.all(r["status"] == 0)
+    assert np.abs(r["acc"] - 1.0).max() < 1e-9
+    assert np.abs(r["y"][0] - 1.0).max() < 1e-9
+
+
+def test_km_dimensionless_form_equals_dimensional_equation():
+    """y2' from C0..C12 equals R'' (2 pi / w1)^2 / R_E of the dimensional
+    Keller-Miksis equation, including the dual-frequency terms."""
+    rng = np.random.default_rng(11)
+    liq = _liq(WATER_CFG)
+    n = 200
+    pA1 = rng.uniform(0.0, 2e5, n)
+    pA2 = rng.uniform(0.0, 1e5, n)
+    f1 = rng.uniform(2e4, 1e6, n)
+    f2 = rng.uniform(1e4, 2e6, n)
+    theta = rng.uniform(0.0, 2 * math.pi, n)
+    RE = rng.uniform(2e-6, 50e-6, n)
+    C = oracle.km_coefficients(pA1, f1, pA2, f2, theta, RE, liq)
+    y1 = rng.uniform(0.3, 4.0, n)
+    y2 = rng.uniform(-3.0, 3.0, n)
+    tau = rng.uniform(0.0, 1.0, n)
+    dy = oracle.rhs(oracle.KM, C, tau, np.stack([y1, y2]))
+    assert np.array_equal(dy[0], y2)
+    for i in range(n):
+        w1 = 2 * math.pi * f1[i]
+        R = y1[i] * RE[i]
+        Rd = y2[i] * RE[i] * w1 / (2 * math.pi)
+        t = tau[i] * 2 * math.pi / w1
+        rdd = oracle.km_dimensional_rdd(R, Rd, t, pA1[i], f1[i], pA2[i], f2[i], theta[i], RE[i], liq)
+        ref = rdd * (2 * math.pi / w1) ** 2 / RE[i]
+        assert abs(dy[1, i] - ref) <= 1e-10 * max(1.0, abs(ref)), (i, dy[1, i], ref)
+
+
+def test_km_small_amplitude_response_matches_linearisation():
+    """For small P_A the radius follows the linearised equation about (1, 0),
+    integrated here independently with SciPy; the gap is O(P_A^2)."""
+    from scipy.integrate import solve_ivp
+
+    liq = _liq(WATER_CFG)
+    f = 1e5
+    T = 3.0
+    gaps = []
+    for pA in (50.0, 100.0):
+        C = oracle.km_coefficients(pA, f, 0.0, 0.0, 0.0, 10e-6, liq)[:, 0]
+        # first-order Taylor expansion of N_KM / D_KM about y1 = 1, y2 = 0
+        D0 = 1.0 + C[4] * C[9]
+        kx = (C[3] - C[0] * C[10]) / D0
+        kv = (C[1] - C[2] * C[9] - C[4]) / D0
+
+        def lin(t, z):
+            x, v = z
+            force = -(C[5] * math.sin(2 * math.pi * t) + C[7] * math.cos(2 * math.pi * t)) / D0
+            return [v, kx * x + kv * v + force]
+
+        taus = np.linspace(0.25, T, 12)
+        sol = solve_ivp(lin, (0.0, T), [0.0, 0.0], method="DOP853", rtol=1e-12, atol=1e-16,
+                        t_eval=taus)
+        x_nl = []
+        for tt in taus:
+            tol = oracle.make_tol(rtol=1e-12, atol=1e-14, dt0=1e-3, dt_min=1e-16, dt_max=1e-2,
+                                  t0=0.0, t1=float(tt))
+            r = oracle.cashkarp_solve(oracle.KM, C[:, None], [[1.0], [0.0]], tol)
+            x_nl.append(r["y"][0, 0] - 1.0)
+        x_nl = np.array(x_nl)
+        amp = np.abs(sol.y[0]).max()
+        assert amp > 0
+        gaps.append(np.abs(x_nl - sol.y[0]).max() / amp)
+    assert gaps[0] < 2e-3
+    assert 1.6 < gaps[1] / gaps[0] < 2.5        # relative gap grows linearly in P_A
+
+
+def test_km_function_evaluations_near_paper_table():
+    """RHS evaluation counts at T = 1e-10 against the paper's MPGOS numbers
+    (Table NumberFunctionEvaluation); the controller is unspecified there, so
+    agreement within 15% is required, not equality."""
+    g = json.load(open(os.path.join(GOLDEN, "km_function_evaluations.json")))
+    liq = _liq(g["liquid"])
+    f = np.array(g["f1_Hz"])
+    C = oracle.km_coefficients(g["pA1_Pa"], f, 0.0, 0.0, 0.0, g["RE_m"], liq)
+    tol = oracle.make_tol(rtol=g["tol"], atol=g["tol"], dt0=1e-2, dt_min=1e-14, dt_max=1e-1,
+                          t0=0.0, t1=g["tau_end"])
+    r = oracle.cashkarp_solve(oracle.KM, C, np.stack([np.ones(3), np.zeros(3)]), tol)
+    ratio = r["nrhs"] / np.array(g["nf_mpgos"])
+    assert np.all(np.abs(ratio - 1.0) < 0.15), ratio
+
+
+def test_km_global_error_tracks_tolerance():
+    """E = |y1(2) - y1^E(2)| against a T = 1e-15 run (Sec. 4.2.2 method)."""
+    g = json.load(open(os.path.join(GOLDEN, "km_function_evaluations.json")))
+    liq = _liq(g["liquid"])
+    f = np.array(g["f1_Hz"])
+    C = oracle.km_coefficients(g["pA1_Pa"], f, 0.0, 0.0, 0.0, g["RE_m"], liq)
+    y0 = np.stack([np.ones(3), np.zeros(3)])
+
+    def run(tv):
+        tol = oracle.make_tol(rtol=tv, atol=tv, dt0=1e-2, dt_min=1e-16, dt_max=1e-1, t0=0.0, t1=2.0)
+        return oracle.cashkarp_solve(oracle.KM, C, y0, tol)["y"][0]
+
+    ref = run(1e-15)
+    e_prev = None
+    for tv in (1e-12, 1e-10, 1e-8):
+        e = np.abs(run(tv) - ref)
+        assert np.all(e < 30 * tv), (tv, e)
+        if e_prev is not None:
+            assert np.all(e > e_prev)
+        e_prev = e
+
+
+# ---------------------------------------------------------------------------
+# pressure relief valve (Sec. 4.3) and the event machinery
+# ---------------------------------------------------------------------------
+
+PRV = dict(kappa=1.25, delta=10.0, beta=20.0, r=0.8)
+
+
+def _prv_params(q):
+    q = np.atleast_1d(np.asarray(q, dtype=float))
+    one = np.ones_like(q)
+    return np.stack([q, PRV["kappa"] * one, PRV["delta"] * one, PRV["beta"] * one, PRV["r"] * one])
+
+
+def _prv_tol(t1=1024.0, acc_t_start=512.0):
+    return oracle.make_tol(rtol=1e-10, atol=1e-10, dt0=1e-3, dt_min=1e-14, dt_max=1.0,
+                           event_tol=1e-6, t0=0.0, t1=t1, acc_t_start=acc_t_start)
+
+
+def test_prv_equilibrium_is_stationary():
+    """y1*^2 (y1* + delta) = q^2, y2 = 0, y3 = y1* + delta is a fixed point."""
+    for q in (0.5, 3.0, 9.0):
+        roots = np.roots([1.0, PRV["delta"], 0.0, -q * q])
+        y1s = float(max(r.real for r in roots if abs(r.imag) < 1e-12))
+        yeq = np.array([[y1s], [0.0], [y1s + PRV["delta"]]])
+        dy = oracle.rhs(oracle.PRV, _prv_params(q), 0.0, yeq)
+        assert np.abs(dy).max() < 1e-12 * 20
+
+
+def test_prv_bifurcation_impacting_range():
+    """The valve hits the seat (min y1 = 0) for q up to about 7.5 and not
+    beyond (Sec. 4.3, bifurcation diagram)."""
+    q = np.array([0.3, 1.0, 3.0, 5.0, 7.0, 8.5, 9.5])
+    n = q.size
+    y0 = np.stack([np.full(n, 0.2), np.zeros(n), np.zeros(n)])
+    r = oracle.cashkarp_solve(oracle.PRV, _prv_params(q), y0, _prv_tol(), nthreads=0)
+    assert np.all(r["status"] == 0)
+    ymin = r["acc"][32]
+    nimp = r["acc"][34]
+    impacting = q < 7.5
+    assert np.all(ymin[impacting] == 0.0)
+    assert np.all(nimp[impacting] > 10)
+    assert np.all(ymin[~impacting] > 0.05)
+    assert np.all(r["y"][2] >= 0.0)
+    assert np.all(r["t"] == 1024.0)
+
+
+def test_bouncing_ball_event_location_and_impact_law():
+    """Ball: y1'' = -g, impact y2+ = -r y2-.  Apex heights after k bounces are
+    r^(2k) h0 and the k-th impact time is sqrt(2h0/g)(1 + 2 sum_{j<k} r^j)."""
+    g, rr, h0 = 1.0, 0.8, 1.0
+    T = 10.0
+    tol = oracle.make_tol(rtol=1e-10, atol=1e-10, dt0=1e-3, dt_min=1e-14, dt_max=1.0,
+                          event_tol=1e-6, t0=0.0, t1=T, acc_t_start=0.0)
+    r = oracle.cashkarp_solve(oracle.BALL, [[g], [rr]], [[h0], [0.0], [0.0]], tol)
+    assert r["status"][0] == 0
+    t_imp = [math.sqrt(2 * h0 / g)]
+    while True:
+        k = len(t_imp)
+        nxt = t_imp[-1] + 2 * rr ** k * math.sqrt(2 * h0 / g)
+        if nxt > T:
+            break
+        t_imp.append(nxt)
+    n_imp = int(r["acc"][34, 0])
+    n_max = int(r["acc"][33, 0])
+    assert n_imp == len(t_imp)
+    # apexes between impacts (the start apex at t = 0 is not a crossing)
+    assert n_max in (n_imp - 1, n_imp)
+    for m in range(min(n_max, oracle.RING)):
+        h = r["acc"][m, 0]
+        assert abs(h - rr ** (2 * (m + 1)) * h0) < 1e-5 * h0, (m, h)
+    assert r["acc"][32, 0] == 0.0           # it touched the floor
+
+
+def test_prv_impacts_keep_body_on_or_above_seat():
+    q = np.array([0.5, 2.0, 6.0])
+    y0 = np.stack([np.full(3, 0.2), np.zeros(3), np.zeros(3)])
+    r = oracle.cashkarp_solve(oracle.PRV, _prv_params(q), y0, _prv_tol(t1=200.0, acc_t_start=0.0))
+    assert np.all(r["acc"][32] >= -1e-6)     # within the event tolerance
