@@ -1,0 +1,259 @@
+/*
+ * ens.h -- C ABI of the GB300-native ensemble ODE solver.
+ *
+ * The library integrates very many independent, low-dimensional, non-stiff
+ * ODE systems, one parameter set each, the workload of Nagy, Plavecz &
+ * Hegedus, arXiv 2011.01740 ("Solving large number of non-stiff,
+ * low-dimensional ordinary differential equation systems on GPUs and CPUs").
+ * One GPU thread owns one system at a time (the "per-thread approach",
+ * Sec. 3.2.1); state, Runge-Kutta stages and parameters live in registers.
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are structure-of-arrays: element k of system i sits at
+ *     [k * n + i].  All floating-point data are IEEE double.
+ *   - Input pointers may be host or device memory (told apart with
+ *     cudaPointerGetAttributes); the library copies what it needs and the
+ *     caller keeps ownership.  Output buffers are caller-owned; `dst` of
+ *     ens_read may likewise be host or device memory.
+ *   - Every call returns an ens_status.  Nothing aborts, traps or prints; the
+ *     text of the last failure is available through ens_last_error.  Per-system
+ *     failures (step-size underflow, step budget, ...) are reported as status
+ *     words (ENS_SYS_*), not as call failures.
+ *   - A context is bound to the CUDA device that was current at ens_create and
+ *     must be used from one host thread at a time.
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).  Work is enqueued asynchronously; ens_sync waits.
+ */
+#ifndef ENS_H
+#define ENS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ens_ctx ens_ctx;
+
+/* Call status. */
+typedef enum {
+    ENS_OK = 0,
+    ENS_EINVAL = 1,    /* bad argument (sizes, enums, NULL pointers, tolerances) */
+    ENS_ENOMEM = 2,    /* device or host allocation failed                        */
+    ENS_ECUDA = 3,     /* a CUDA runtime call failed (message in ens_last_error)   */
+    ENS_ETIMEOUT = 4,  /* the solve hit its wall-clock budget (systems flagged)    */
+    ENS_ESYSTEM = 5,   /* the solve finished but some systems carry a status word  */
+    ENS_ENOTSUP = 6    /* combination not supported (e.g. RK4 with events)         */
+} ens_status;
+
+/* Built-in right-hand sides (inlined device functions).
+ *   ENS_SYS_TOY_X2P        x' = x^2 - p                      (Sec. 3, Eq. exemplary_system)
+ *                          dim 1, params [p]
+ *   ENS_SYS_LORENZ         x1' = sigma (x2 - x1), x2' = rho x1 - x2 - x1 x3,
+ *                          x3' = x1 x2 - b x3                (Sec. 4.1, Eqs. Lorenz1-3)
+ *                          dim 3, params [rho, sigma, b]
+ *   ENS_SYS_KELLER_MIKSIS  dimensionless Keller-Miksis, y1' = y2, y2' = N_KM / D_KM
+ *                          (Sec. 4.2, Eqs. dimensionless_system1-2, numerator,
+ *                          denominator); dim 2, params [C0..C12] (Eq. coefficients,
+ *                          see ens_km_coefficients); tau is the phase-local time.
+ *   ENS_SYS_RELIEF_VALVE   y1' = y2, y2' = -kappa y2 - (y1 + delta) + y3,
+ *                          y3' = beta (q - y1 sqrt(y3))     (Sec. 4.3, Eqs.
+ *                          pressure_relief_valve_1-3) with the impact law
+ *                          y1 <- 0, y2 <- -r y2 (Eqs. impact_law_1-3);
+ *                          dim 3, params [q, kappa, delta, beta, r]          */
+typedef enum {
+    ENS_SYS_TOY_X2P = 0,
+    ENS_SYS_LORENZ = 1,
+    ENS_SYS_KELLER_MIKSIS = 2,
+    ENS_SYS_RELIEF_VALVE = 3
+} ens_system;
+
+/* Steppers: classic RK4 with fixed steps (Sec. 3, Sec. 4.1) and the adaptive
+ * Cash-Karp 4(5) pair with error control (Sec. 4.2.1, Sec. 4.3.1; tableau of
+ * Cash & Karp, ACM TOMS 16(3), 1990). */
+typedef enum { ENS_RK4 = 0, ENS_RKCK45 = 1 } ens_solver;
+
+/* Arithmetic of the kernels.
+ *   ENS_FP64         IEEE double with fused multiply-add (the default path).
+ *   ENS_FP64_STRICT  IEEE double, no contraction, operations in the order the
+ *                    equations are written: bit-reproducible against a plain
+ *                    C evaluation of the same formulas (RK4 systems only).
+ *   ENS_FP32_COMP    right-hand side and stage sums in float with compensated
+ *                    (Kahan) stage combination and a float-pair (hi + lo)
+ *                    state; time, error norm, controller and event root in
+ *                    double (Keller-Miksis / Cash-Karp only).               */
+typedef enum { ENS_FP64 = 0, ENS_FP32_COMP = 1, ENS_FP64_STRICT = 2 } ens_precision;
+
+/* Per-system status bits (ENS_STATUS). */
+enum {
+    ENS_SYS_DT_UNDERFLOW = 1,        /* rejected step proposal fell below dt_min  */
+    ENS_SYS_MAX_STEPS = 2,           /* trial-step budget max_steps exhausted      */
+    ENS_SYS_NONFINITE = 4,           /* final state not finite (fixed-step solve)  */
+    ENS_SYS_EVENT_NO_CONVERGE = 8,   /* more than 40 event-location retries        */
+    ENS_SYS_TIMEOUT = 16             /* solve budget timeout_s ran out             */
+};
+
+/* ens_read selectors and the layout each returns (n = ensemble size). */
+enum {
+    ENS_STATE = 0,    /* double [dim][n]   state at the end of the solve          */
+    ENS_ACC = 1,      /* double [rows][n]  accessories, see ens_acc_rows          */
+    ENS_STATUS = 2,   /* int32  [n]        ENS_SYS_* bits                         */
+    ENS_NSTEPS = 3,   /* int64  [n]        accepted steps                         */
+    ENS_NREJ = 4,     /* int64  [n]        steps rejected by the error test       */
+    ENS_NRHS = 5,     /* int64  [n]        right-hand-side evaluations            */
+    ENS_TIME = 6,     /* double [n]        final time (phase-local for phases)    */
+    ENS_DT = 7        /* double [n]        final step-size proposal               */
+};
+
+/* Solver settings.
+ *   rtol, atol     error test: accept iff max_i |y5_i - y4_i| /
+ *                  (atol + rtol max(|y_i|, |y5_i|)) <= 1.  The new step is
+ *                  h * clamp(0.9 E^(-1/5), 0.2, 5) bounded by [dt_min, dt_max]
+ *                  (the paper states tolerances only; this controller is the
+ *                  library's reading).
+ *   dt0            first step (adaptive) or the fixed step (RK4).
+ *   n_steps        RK4 only: number of fixed steps (t_span[1] is ignored).
+ *   event_tol      absolute event tolerance (relief valve, Sec. 4.3.1).
+ *   max_steps      cap on trial steps per system (ENS_SYS_MAX_STEPS).
+ *   n_phases       > 0: phase mode (Keller-Miksis, Sec. 4.2): n_phases
+ *                  integrations over tau in [t_span[0], t_span[0] + phase_len],
+ *                  tau reset at each phase start; accessories per phase.
+ *   acc_t_start    relief valve: the y1 minimum accessory covers t >= it.
+ *   prec           ens_precision.
+ *   timeout_s      wall-clock budget of one ens_solve on the device; systems
+ *                  still running are stopped with ENS_SYS_TIMEOUT (<= 0: 600 s). */
+typedef struct {
+    double rtol, atol;
+    double dt0, dt_min, dt_max;
+    double event_tol;
+    int64_t max_steps;
+    int64_t n_steps;
+    int32_t n_phases;
+    int32_t prec;
+    double phase_len;
+    double acc_t_start;
+    double timeout_s;
+} ens_tol;
+
+/* Launch configuration (see ens_set_launch / ens_autotune).
+ *   mode           ENS_LAUNCH_PLAIN: one system per thread, grid covers n.
+ *                  ENS_LAUNCH_PERSISTENT: a fixed grid of lanes; every lane
+ *                  claims its next system from a device counter (atomicAdd)
+ *                  when its current one finishes (work stealing), so uneven
+ *                  adaptive step counts do not idle warps.
+ *   block          threads per block (multiple of 32, 32..1024).
+ *   blocks_per_sm  persistent mode: resident blocks per SM (grid = SMs x this).
+ *   use_graph      capture the launch sequence of ens_solve in a CUDA graph on
+ *                  the first call and replay it afterwards.
+ *   cost_order     persistent mode: claim systems in decreasing order of their
+ *                  step count in a one-phase pilot solve (longest first). */
+enum { ENS_LAUNCH_PLAIN = 0, ENS_LAUNCH_PERSISTENT = 1 };
+typedef struct {
+    int32_t mode;
+    int32_t block;
+    int32_t blocks_per_sm;
+    int32_t use_graph;
+    int32_t cost_order;
+    int32_t reserved[3];
+} ens_launch;
+
+/* Liquid and gas constants of the Keller-Miksis model (SI units):
+ * density rho_L, sound speed c_L, viscosity mu_L, surface tension sigma,
+ * vapour pressure p_V, ambient pressure P_inf, polytropic exponent gamma. */
+typedef struct {
+    double rho, c, mu, sigma, pv, pinf, gamma;
+} ens_liquid;
+
+/* ------------------------------------------------------------------------ */
+
+/* Create a solver context for n systems of kind `sys`.
+ *   params   SoA [npar][n] (host or device), copied.
+ *   y0       SoA [dim][n]  (host or device), copied: the state at t_span[0].
+ *   t_span   {t0, t1} on the host: integration interval (event mode / plain
+ *            adaptive), or t0 = phase start for phase mode.
+ *   solver   ens_solver; tol: settings above (copied).
+ * n = 0 is valid (every later call is a no-op).  Errors: ENS_EINVAL for a
+ * NULL out/params/y0/tol (when n > 0), unknown enums, non-positive tolerances
+ * or steps; ENS_ENOMEM; ENS_ECUDA.  On failure *out is NULL. */
+ens_status ens_create(ens_ctx **out, ens_system sys, int64_t n, const double *params,
+                      const double *y0, const double t_span[2], ens_solver solver,
+                      const ens_tol *tol);
+
+/* Replace the parameters and initial states of an existing context (same
+ * layout and sizes as ens_create; host or device pointers), enqueued on
+ * `stream`.  Either pointer may be NULL to keep the current values. */
+ens_status ens_set_inputs(ens_ctx *ctx, const double *params, const double *y0, void *stream);
+
+/* Select the launch configuration.  NULL restores the built-in default. */
+ens_status ens_set_launch(ens_ctx *ctx, const ens_launch *cfg);
+
+/* Read back the launch configuration in use. */
+ens_status ens_get_launch(const ens_ctx *ctx, ens_launch *cfg);
+
+/* Integrate every system from its initial state (the inputs are not
+ * modified, so repeated calls give repeated results).  Asynchronous on
+ * `stream`; results become readable in stream order. */
+ens_status ens_solve(ens_ctx *ctx, void *stream);
+
+/* Wait for the context's last solve.  Returns ENS_OK, ENS_ETIMEOUT when any
+ * system hit the wall-clock budget, ENS_ESYSTEM when any system carries
+ * another status bit, or ENS_ECUDA. */
+ens_status ens_sync(ens_ctx *ctx);
+
+/* Copy one output (selector ENS_*) into dst (host or device), which must hold
+ * at least the size the selector's layout gives; dst_bytes smaller than that
+ * is ENS_EINVAL.  Synchronous with respect to the context's last stream. */
+ens_status ens_read(ens_ctx *ctx, int which, void *dst, size_t dst_bytes);
+
+/* Number of accessory rows of ENS_ACC for this context:
+ *   phase mode (Keller-Miksis): 2 * n_phases, row 2k = max y1 in phase k,
+ *     row 2k+1 = min y1 in phase k, taken over the natural step points and the
+ *     phase start (no dense output, Sec. 4.2.1);
+ *   relief valve: 35 rows: rows 0..31 ring of the last Poincare maxima of y1
+ *     (slot m mod 32 holds maximum number m; NaN if unused), row 32 the
+ *     minimum of y1 for t >= acc_t_start, row 33 the number of maxima, row 34
+ *     the number of impacts (Sec. 4.3);
+ *   otherwise 0. */
+int64_t ens_acc_rows(const ens_ctx *ctx);
+
+/* Ensemble size, state dimension and parameter count of a context. */
+int64_t ens_size(const ens_ctx *ctx);
+int32_t ens_dim(const ens_ctx *ctx);
+int32_t ens_npar(const ens_ctx *ctx);
+
+/* Time the candidate launch configurations on this context (plain and
+ * persistent, several block sizes and residencies) with short solves on
+ * `stream`, keep the fastest, and write it to *best (may be NULL).  The
+ * choice is cached per (system, solver, precision, n) for the process. */
+ens_status ens_autotune(ens_ctx *ctx, void *stream, ens_launch *best);
+
+/* Text of the context's last failure ("" if none).  ctx may be NULL: then the
+ * last failure of a call that had no context (ens_create) is returned. */
+const char *ens_last_error(const ens_ctx *ctx);
+
+/* Free the context and its device buffers (NULL is a no-op). */
+void ens_destroy(ens_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Host planner                                                              */
+
+/* Keller-Miksis coefficients C0..C12 of Sec. 4.2 (Eq. coefficients) for n
+ * systems from physical SI parameters: pressure amplitudes pA1, pA2 [Pa],
+ * frequencies f1, f2 [Hz], phase shift theta [rad], equilibrium radius RE [m].
+ * C8 is taken with omega2 (the time derivative of the second driving term);
+ * the printed C8 carries omega1, which is the same whenever pA2 = 0.
+ * All arrays live on the same side (all host or all device); out is SoA
+ * [13][n].  Device arrays are processed by a kernel on `stream`. */
+ens_status ens_km_coefficients(int64_t n, const double *pA1, const double *f1, const double *pA2,
+                               const double *f2, const double *theta, const double *RE,
+                               const ens_liquid *liquid, double *out, void *stream);
+
+/* Library version string. */
+const char *ens_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ENS_H */

@@ -362,8 +362,10 @@ void orc_cashkarp_tableau(double *c, double *a, double *b, double *bs)
 
 /* One Cash-Karp trial step from (t, y) with step h.  k1 = f(t, y) is passed in
  * (it does not change when a step is retried).  Stage i: k_i = f(t + c_i h,
- * y + h sum_j a_ij k_j).  y5 = y + h sum b_i k_i;  y4 = y + h sum bs_i k_i;
- * err = y5 - y4.                                                            */
+ * y + h sum_j a_ij k_j).  y5 = y + h sum b_i k_i, and the error estimate is
+ * the difference of the fifth- and fourth-order solutions written, as Cash &
+ * Karp do, through the weight differences: err = h sum (b_i - bs_i) k_i
+ * (the same quantity as y5 - y4 without the cancellation of forming both).  */
 static void ck_step(int sys, const double *p, int dim, double t, double h, const double *y,
                     const double *k1, double *y5, double *err)
 {
@@ -378,13 +380,13 @@ static void ck_step(int sys, const double *p, int dim, double t, double h, const
         rhs(sys, p, t + CK_c[s] * h, ys, k[s]);
     }
     for (int i = 0; i < dim; ++i) {
-        double s5 = 0.0, s4 = 0.0;
+        double s5 = 0.0, se = 0.0;
         for (int j = 0; j < 6; ++j) {
             s5 = s5 + CK_b[j] * k[j][i];
-            s4 = s4 + CK_bs[j] * k[j][i];
+            se = se + (CK_b[j] - CK_bs[j]) * k[j][i];
         }
         y5[i] = y[i] + h * s5;
-        err[i] = y5[i] - (y[i] + h * s4);
+        err[i] = h * se;
     }
 }
 

@@ -1,0 +1,118 @@
+// common.cuh -- types and helpers shared by the solver kernels and the C ABI.
+//
+// Layout convention (all kernels): structure-of-arrays, element k of system i
+// at [k * n + i], so that one warp touching 32 consecutive systems issues one
+// coalesced 256-byte access per element.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ens.h"
+
+namespace ens {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxPar = 13;
+constexpr int kRing = 32;             // relief valve: Poincare maxima kept
+constexpr int kPrvAccRows = kRing + 3;
+constexpr int kEventRetries = 40;     // consecutive event-location retries allowed
+
+// Per-system status bits (mirror ENS_SYS_* of ens.h).
+constexpr int32_t kStDtUnderflow = ENS_SYS_DT_UNDERFLOW;
+constexpr int32_t kStMaxSteps = ENS_SYS_MAX_STEPS;
+constexpr int32_t kStNonFinite = ENS_SYS_NONFINITE;
+constexpr int32_t kStEventNoConverge = ENS_SYS_EVENT_NO_CONVERGE;
+constexpr int32_t kStTimeout = ENS_SYS_TIMEOUT;
+
+inline int sys_dim(int sys) {
+  switch (sys) {
+    case ENS_SYS_TOY_X2P: return 1;
+    case ENS_SYS_LORENZ: return 3;
+    case ENS_SYS_KELLER_MIKSIS: return 2;
+    case ENS_SYS_RELIEF_VALVE: return 3;
+    default: return 0;
+  }
+}
+
+inline int sys_npar(int sys) {
+  switch (sys) {
+    case ENS_SYS_TOY_X2P: return 1;
+    case ENS_SYS_LORENZ: return 3;
+    case ENS_SYS_KELLER_MIKSIS: return 13;
+    case ENS_SYS_RELIEF_VALVE: return 5;
+    default: return 0;
+  }
+}
+
+// Device scratch of one context: the work-stealing claim counter and the OR
+// of all per-system status words.  Reset to zero before every solve.
+struct Scratch {
+  unsigned long long next;   // next unclaimed position in the claim order
+  unsigned int any_status;   // OR of status words of finished systems
+  unsigned int pad;
+};
+
+// Arguments of the fixed-step kernels.
+struct Rk4Args {
+  int64_t n;
+  const double* params;  // [npar][n]
+  const double* y0;      // [dim][n]
+  double* y;             // [dim][n]
+  double* t_out;         // [n]
+  int32_t* status;       // [n]
+  int64_t* nacc;         // [n]
+  int64_t* nrhs;         // [n]
+  Scratch* scratch;
+  double t0, dt;
+  int64_t nsteps;
+};
+
+// Arguments of the adaptive kernels.
+struct AdaptArgs {
+  int64_t n;
+  const double* params;  // [npar][n]
+  const double* y0;      // [dim][n]
+  double* y;             // [dim][n]
+  double* t_out;         // [n]
+  double* dt_out;        // [n]
+  double* acc;           // [rows][n]
+  int32_t* status;       // [n]
+  int64_t* nacc;         // [n]
+  int64_t* nrej;         // [n]
+  int64_t* nrhs;         // [n]
+  const int32_t* order;  // claim order (persistent mode), may be null
+  Scratch* scratch;
+  double rtol, atol, dt0, dt_min, dt_max, event_tol;
+  double t0, t1, phase_len, acc_t_start;
+  int64_t max_steps;
+  int32_t n_phases;
+  int32_t persistent;
+  uint64_t timeout_ns;
+};
+
+// Nanosecond wall clock of the GPU (PTX %globaltimer).
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Cash & Karp (ACM TOMS 16(3), 1990) embedded 4(5) pair, written as exact
+// rationals; kB* are the fifth-order weights that advance the solution, kD*
+// the differences b - b* of the error estimate (b2 = b*2 = 0, b5 = 0).
+namespace ck {
+constexpr double c2 = 1.0 / 5.0, c3 = 3.0 / 10.0, c4 = 3.0 / 5.0, c5 = 1.0, c6 = 7.0 / 8.0;
+constexpr double a21 = 1.0 / 5.0;
+constexpr double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+constexpr double a41 = 3.0 / 10.0, a42 = -9.0 / 10.0, a43 = 6.0 / 5.0;
+constexpr double a51 = -11.0 / 54.0, a52 = 5.0 / 2.0, a53 = -70.0 / 27.0, a54 = 35.0 / 27.0;
+constexpr double a61 = 1631.0 / 55296.0, a62 = 175.0 / 512.0, a63 = 575.0 / 13824.0,
+                 a64 = 44275.0 / 110592.0, a65 = 253.0 / 4096.0;
+constexpr double b1 = 37.0 / 378.0, b3 = 250.0 / 621.0, b4 = 125.0 / 594.0, b6 = 512.0 / 1771.0;
+constexpr double bs1 = 2825.0 / 27648.0, bs3 = 18575.0 / 48384.0, bs4 = 13525.0 / 55296.0,
+                 bs5 = 277.0 / 14336.0, bs6 = 1.0 / 4.0;
+constexpr double d1 = b1 - bs1, d3 = b3 - bs3, d4 = b4 - bs4, d5 = -bs5, d6 = b6 - bs6;
+}  // namespace ck
+
+}  // namespace ens
