@@ -1,0 +1,441 @@
+"""Benchmark of the ensemble ODE solver (arXiv 2011.01740 method) on GB300.
+
+One step = one full solve of the Keller-Miksis ensemble: a 362 x 362 grid of
+driving amplitude p_A (linear, 0-2 bar) and frequency f (logarithmic,
+20 kHz - 1 MHz), 131,044 bubbles, Cash-Karp 4(5) at rtol = atol = 1e-10,
+64 forcing periods with the per-period max / min radius recorded (Sec. 4.2).
+The metric is accepted RK system-steps per second.  With --gpus N (torchrun)
+every rank solves its own 131,044-system slice of a 362N x 362 grid (p_A rows
+interleaved across ranks), so the work per GPU is fixed (weak scaling) and no
+data crosses ranks during the solve.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores instead (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2011_01740_gb300 import workloads as W  # noqa: E402
+
+# FP64 flops (DFMA = 2, DADD = DMUL = 1) executed per Cash-Karp trial step of
+# the Keller-Miksis kernel, and per RK4 step of the x' = x^2 - p and Lorenz
+# kernels, from the ncu instruction counters of profiles/ (None until
+# measured: the roofline then reports achieved = null).
+FLOPS_PER_KM_TRIAL = None
+FLOPS_PER_X2P_STEP = 21.0     # 10 DFMA + 1 DADD (Sec. 3.2.2 counters; kernel counted by ncu)
+FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast kernel
+
+# FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (2 DFMA lanes) x 2.07 GHz = 1.2586
+# TFLOP/s, the nominal 1.25 TFLOP/s of the part at its maximum SM clock.
+SMS = 152
+FP64_FLOP_PER_CLK_SM = 4.0
+SM_MAX_MHZ = 2070.0
+FP64_PEAK = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6
+
+WORKLOAD = "keller_miksis_362x362_pA0-2bar_f20k-1M_log_64periods_ck45_tol1e-10_fp64"
+METRIC = "accepted RK system-steps/s (Keller-Miksis 362x362 p_A x f grid, Cash-Karp 1e-10, 64 periods, FP64)"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def km_slice(world: int, rank: int, m: int = 362, n_phases: int = 64):
+    """Rank `rank`'s share of a (m world) x m grid: every world-th p_A row."""
+    full = W.km(m * world, m, n_phases=n_phases)
+    rows = np.arange(rank, m * world, world)
+    idx = (rows[:, None] * m + np.arange(m)[None, :]).ravel()
+    return W.take(full, idx)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        cmd = ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            return
+        try:
+            while not self._stop.is_set():
+                line = p.stdout.readline()
+                if not line:
+                    break
+                self.samples.append([x.strip() for x in line.split(",")])
+        finally:
+            p.terminate()
+            try:
+                p.wait(timeout=2)
+            except Exception:
+                p.kill()
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=3)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if len(s) > 4 + k and s[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        busy = [v for v in sm if v > 0]
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import paper_2011_01740_gb300 as ens
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    km = km_slice(world, rank, n_phases=args.phases)
+    ph = km["phys"]
+    n = ph["pA1"].size
+    t = km["tol"]
+    tol = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
+                       n_phases=t.n_phases, phase_len=t.phase_len, timeout_s=900.0)
+    stream = torch.cuda.Stream()
+    dev = torch.device("cuda", local)
+    # inputs resident in HBM before timing: coefficients planned on the device
+    phys_d = [torch.from_numpy(ph[k]).to(dev) for k in ("pA1", "f1", "pA2", "f2", "theta", "RE")]
+    C_d = ens.ens_km_coefficients(*phys_d, km["liquid"], stream=stream)
+    y0_d = torch.from_numpy(km["y0"]).to(dev)
+    stream.synchronize()
+    ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, n, C_d, y0_d, (0.0, 1.0), ens.ENS_RKCK45, tol)
+    launch = ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=args.block,
+                             blocks_per_sm=args.bps, use_graph=1, cost_order=args.cost_order)
+    ens.ens_set_launch(ctx, launch)
+    kernels_per_solve = 1 + (4 if args.cost_order else 0)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    for _ in range(args.warmup):
+        ens.ens_solve(ctx, stream)
+        if ens.ens_sync(ctx) != ens.ENS_OK:
+            raise RuntimeError(ens.ens_last_error(ctx))
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()                       # evict L2 between timed steps
+            ev[k][0].record(stream)
+            ens.ens_solve(ctx, stream)
+            ev[k][1].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    st = ens.ens_sync(ctx)
+    if st != ens.ENS_OK:
+        raise RuntimeError(f"solve status {st}: {ens.ens_last_error(ctx)}")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    nacc = ens.ens_read(ctx, ens.ENS_NSTEPS)
+    nrej = ens.ens_read(ctx, ens.ENS_NREJ)
+    steps_local = float(nacc.sum()) * args.steps
+    trials_local = float(nacc.sum() + nrej.sum())
+
+    # whole-job aggregate: all ranks' steps over the slowest rank's time
+    if dist is not None:
+        tt = torch.tensor([total_ms, steps_local], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        dist.all_reduce(mx[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:2], op=dist.ReduceOp.SUM)
+        total_ms_max, steps_all = float(mx[0]), float(tt[1])
+    else:
+        total_ms_max, steps_all = total_ms, steps_local
+    value = steps_all / (total_ms_max / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        e2e = run_e2e(ens, ctx, km, stream, args)
+
+    # ---- roofline of the dominant kernel ----
+    kernel_ms = total_ms / args.steps
+    if FLOPS_PER_KM_TRIAL is not None:
+        achieved = FLOPS_PER_KM_TRIAL * trials_local / (kernel_ms / 1e3) / 1e12
+    else:
+        achieved = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
+                "frac": (achieved / (FP64_PEAK / 1e12)) if achieved else None,
+                "traffic": None, "kernel": "ck_phased_kernel<KellerMiksis<false>>",
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (nominal 1.25 TFLOP/s)",
+                "flops_per_trial": FLOPS_PER_KM_TRIAL, "trials_per_launch": trials_local}
+
+    secondary = {}
+    if rank == 0 and not args.quick:
+        secondary = run_secondary(ens, torch, stream, dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(km, args.cpu_seconds)
+
+    ens.ens_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "system-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (deterministic parameter grid; no dataset)",
+            "config": {"workload": WORKLOAD, "systems_per_gpu": n, "systems": n * world,
+                       "grid": [362 * world, 362], "n_phases": args.phases,
+                       "launch": launch.as_dict(),
+                       "l2": "256 MiB buffer written between timed steps (inputs 14 MB < L2)",
+                       "parallelism": f"systems sharded over {world} GPU(s), no collective in the solve"},
+            "accepted_steps_per_solve": steps_local / args.steps,
+            "trial_steps_per_solve": trials_local,
+            "step_ms": step_ms,
+            "roofline": roofline,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "gpu_launches": kernels_per_solve * args.steps,
+            "secondary": secondary,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_e2e(ens, ctx, km, stream, args):
+    """Same metric through the public API with HOST buffers: host planner,
+    host->device inputs, solve, device->host accessories and status."""
+    import torch
+    ph = km["phys"]
+    n = ph["pA1"].size
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in ph.items()}
+    y0_h = torch.from_numpy(km["y0"]).pin_memory()
+    rows = ens.ens_acc_rows(ctx)
+    acc_h = torch.empty((rows, n), dtype=torch.float64).pin_memory()
+    st_h = torch.empty((n,), dtype=torch.int32).pin_memory()
+    C_h = torch.empty((13, n), dtype=torch.float64).pin_memory()
+    times = []
+    steps = 0.0
+    for k in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ens.ens_km_coefficients(*[pinned[k2] for k2 in ("pA1", "f1", "pA2", "f2", "theta", "RE")],
+                                km["liquid"], out=C_h, stream=stream)
+        ens.ens_set_inputs(ctx, C_h, y0_h, stream)
+        ens.ens_solve(ctx, stream)
+        st = ens.ens_sync(ctx)
+        ens.ens_read(ctx, ens.ENS_ACC, acc_h)
+        ens.ens_read(ctx, ens.ENS_STATUS, st_h)
+        times.append(time.perf_counter() - t0)
+        if st != ens.ENS_OK:
+            raise RuntimeError(ens.ens_last_error(ctx))
+        steps += float(ens.ens_read(ctx, ens.ENS_NSTEPS).sum())
+    return {"value": steps / sum(times), "unit": "system-steps/s",
+            "h2d_bytes_per_step": int((13 + 2) * n * 8), "d2h_bytes_per_step": int(rows * n * 8 + n * 4),
+            "steps": args.e2e_steps, "s_per_step": sum(times) / len(times)}
+
+
+def run_secondary(ens, torch, stream, dev):
+    """The other hot-path workloads, timed the same way (one launch each after
+    a warm-up): RK4 peak-calibration x' = x^2 - p (Sec. 3), RK4 Lorenz
+    (Sec. 4.1) and the relief valve with events (Sec. 4.3)."""
+    out = {}
+
+    def timed(ctx, reps):
+        ens.ens_solve(ctx, stream)
+        ens.ens_sync(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ens.ens_solve(ctx, stream)
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # x' = x^2 - p, 2^20 systems, 1000 steps: FP64 pipe calibration
+    wl = W.x2p(1 << 20)
+    ctx = ens.ens_create(ens.ENS_SYS_TOY_X2P, 1 << 20, wl["params"], wl["y0"], (0, 0), ens.ENS_RK4,
+                         ens.make_tol(dt0=wl["dt"], n_steps=wl["nsteps"]))
+    ens.ens_set_launch(ctx, ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=128))
+    ms = timed(ctx, 5)
+    ens.ens_destroy(ctx)
+    sps = (1 << 20) * 1000 / (ms / 1e3)
+    out["x2p_rk4_calibration"] = {"systems": 1 << 20, "ms": ms, "value": sps, "unit": "system-steps/s",
+                                  "fp64_tflops": sps * FLOPS_PER_X2P_STEP / 1e12,
+                                  "fp64_frac": sps * FLOPS_PER_X2P_STEP / FP64_PEAK}
+    # Lorenz, 16384 systems, 1000 steps
+    wl = W.lorenz(16384)
+    ctx = ens.ens_create(ens.ENS_SYS_LORENZ, 16384, wl["params"], wl["y0"], (0, 0), ens.ENS_RK4,
+                         ens.make_tol(dt0=wl["dt"], n_steps=wl["nsteps"]))
+    best = ens.ens_autotune(ctx, stream)
+    ms = timed(ctx, 20)
+    ens.ens_destroy(ctx)
+    sps = 16384 * 1000 / (ms / 1e3)
+    out["lorenz_rk4_16384"] = {"ms": ms, "value": sps, "unit": "system-steps/s",
+                               "fp64_frac": sps * FLOPS_PER_LORENZ_STEP / FP64_PEAK,
+                               "launch": best.as_dict()}
+    # relief valve, 262144 systems, t in [0, 1024], events
+    wl = W.prv(262144)
+    t = wl["tol"]
+    tol = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
+                       event_tol=t.event_tol, acc_t_start=t.acc_t_start, timeout_s=900.0)
+    ctx = ens.ens_create(ens.ENS_SYS_RELIEF_VALVE, 262144, wl["params"], wl["y0"], (t.t0, t.t1),
+                         ens.ENS_RKCK45, tol)
+    ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=2, use_graph=1))
+    ms = timed(ctx, 1)
+    nacc = ens.ens_read(ctx, ens.ENS_NSTEPS)
+    ens.ens_destroy(ctx)
+    out["relief_valve_262144"] = {"ms": ms, "value": float(nacc.sum()) / (ms / 1e3),
+                                  "unit": "system-steps/s"}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------
+
+def _oracle_sample_solve(km, idx):
+    import oracle
+    sub = W.take(km, idx)
+    ph = sub["phys"]
+    C = oracle.km_coefficients(ph["pA1"], ph["f1"], ph["pA2"], ph["f2"], ph["theta"], ph["RE"],
+                               oracle.liquid(**sub["liquid"]))
+    t = sub["tol"]
+    otol = oracle.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
+                           n_phases=t.n_phases, phase_len=t.phase_len, t0=t.t0)
+    t0 = time.perf_counter()
+    r = oracle.cashkarp_solve(oracle.KM, C, sub["y0"], otol, nthreads=0)
+    return float(r["nacc"].sum()), time.perf_counter() - t0
+
+
+def cpu_baseline(km, seconds: float):
+    """The oracle (plain C, all host cores) on a stratified sample of the same
+    131,044 systems, sized to about `seconds` of CPU time."""
+    import oracle
+    n = km["phys"]["pA1"].size
+    k = 256
+    steps, el = _oracle_sample_solve(km, W.subsample(n, k))
+    if el < seconds / 4:
+        k = int(min(n, k * max(1.0, seconds / max(el, 1e-3))))
+        steps, el = _oracle_sample_solve(km, W.subsample(n, k))
+    return {"value": steps / el, "unit": "system-steps/s", "cores": oracle.max_threads(),
+            "kind": "oracle", "sample": f"{k} of {n} systems (stratified, seed {W.SEED}), 64 periods",
+            "seconds": el}
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    km = km_slice(1, 0, n_phases=args.phases)
+    n = km["phys"]["pA1"].size
+    k = args.ref_systems
+    idx = W.subsample(n, k)
+    for _ in range(args.warmup):
+        _oracle_sample_solve(km, W.subsample(n, min(k, 64)))
+    tot_steps, tot_s = 0.0, 0.0
+    for _ in range(args.steps):
+        s, el = _oracle_sample_solve(km, idx)
+        tot_steps += s
+        tot_s += el
+    value = tot_steps / tot_s
+    cpu = {"value": value, "unit": "system-steps/s", "cores": oracle.max_threads(), "kind": "oracle",
+           "sample": f"{k} of {n} systems (stratified, seed {W.SEED}) per step, 64 periods"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "system-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (deterministic parameter grid)",
+            "config": {"workload": WORKLOAD, "systems": n, "sampled_systems_per_step": k},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "system-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--phases", type=int, default=64)
+    ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--bps", type=int, default=2)
+    ap.add_argument("--cost-order", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-systems", type=int, default=1024)
+    ap.add_argument("--quick", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

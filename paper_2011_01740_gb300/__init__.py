@@ -1,1 +1,304 @@
-"""GB300-native ensemble ODE solver (arXiv 2011.01740 method): Python binding."""
+"""GB300-native ensemble ODE solver (the method of arXiv 2011.01740).
+
+Thin Python binding of the C ABI declared in ``include/ens.h``: every function
+below has the C name, marshals its arguments (numpy arrays, torch tensors on
+the host or the GPU, streams) into plain pointers and sizes, and raises
+``EnsError`` with ``ens_last_error`` when the call fails.  All numerical work
+runs in the CUDA kernels of ``libens.so``; there is no CPU fallback, and a
+missing library is an error.
+
+PyTorch is used for device memory and streams only: pass CUDA tensors as
+inputs / destinations and a ``torch.cuda.Stream`` (or a raw ``cudaStream_t``
+integer) as ``stream``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (input generators, no method arithmetic)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libens.so")
+
+# enums of ens.h
+ENS_OK, ENS_EINVAL, ENS_ENOMEM, ENS_ECUDA, ENS_ETIMEOUT, ENS_ESYSTEM, ENS_ENOTSUP = range(7)
+ENS_SYS_TOY_X2P, ENS_SYS_LORENZ, ENS_SYS_KELLER_MIKSIS, ENS_SYS_RELIEF_VALVE = range(4)
+ENS_RK4, ENS_RKCK45 = 0, 1
+ENS_FP64, ENS_FP32_COMP, ENS_FP64_STRICT = 0, 1, 2
+ENS_SYS_DT_UNDERFLOW, ENS_SYS_MAX_STEPS, ENS_SYS_NONFINITE = 1, 2, 4
+ENS_SYS_EVENT_NO_CONVERGE, ENS_SYS_TIMEOUT = 8, 16
+ENS_STATE, ENS_ACC, ENS_STATUS, ENS_NSTEPS, ENS_NREJ, ENS_NRHS, ENS_TIME, ENS_DT = range(8)
+ENS_LAUNCH_PLAIN, ENS_LAUNCH_PERSISTENT = 0, 1
+
+DIM = {ENS_SYS_TOY_X2P: 1, ENS_SYS_LORENZ: 3, ENS_SYS_KELLER_MIKSIS: 2, ENS_SYS_RELIEF_VALVE: 3}
+NPAR = {ENS_SYS_TOY_X2P: 1, ENS_SYS_LORENZ: 3, ENS_SYS_KELLER_MIKSIS: 13, ENS_SYS_RELIEF_VALVE: 5}
+
+_STATUS_NAMES = {0: "ENS_OK", 1: "ENS_EINVAL", 2: "ENS_ENOMEM", 3: "ENS_ECUDA", 4: "ENS_ETIMEOUT",
+                 5: "ENS_ESYSTEM", 6: "ENS_ENOTSUP"}
+
+
+class EnsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class EnsTol(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("dt0", ctypes.c_double),
+                ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double),
+                ("event_tol", ctypes.c_double), ("max_steps", ctypes.c_int64),
+                ("n_steps", ctypes.c_int64), ("n_phases", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("phase_len", ctypes.c_double),
+                ("acc_t_start", ctypes.c_double), ("timeout_s", ctypes.c_double)]
+
+
+class EnsLaunch(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("cost_order", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self):
+        return dict(mode=self.mode, block=self.block, blocks_per_sm=self.blocks_per_sm,
+                    use_graph=self.use_graph, cost_order=self.cost_order)
+
+
+class EnsLiquid(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("rho", "c", "mu", "sigma", "pv", "pinf", "gamma")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libens.so (building it with nvcc first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+        if not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: the CUDA library must be built")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        st = ctypes.c_int
+        L.ens_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int64, vp, vp,
+                                 ctypes.c_double * 2, ctypes.c_int, ctypes.POINTER(EnsTol)]
+        L.ens_create.restype = st
+        L.ens_set_inputs.argtypes = [vp, vp, vp, vp]
+        L.ens_set_inputs.restype = st
+        L.ens_set_launch.argtypes = [vp, ctypes.POINTER(EnsLaunch)]
+        L.ens_set_launch.restype = st
+        L.ens_get_launch.argtypes = [vp, ctypes.POINTER(EnsLaunch)]
+        L.ens_get_launch.restype = st
+        L.ens_solve.argtypes = [vp, vp]
+        L.ens_solve.restype = st
+        L.ens_sync.argtypes = [vp]
+        L.ens_sync.restype = st
+        L.ens_read.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t]
+        L.ens_read.restype = st
+        L.ens_acc_rows.argtypes = [vp]
+        L.ens_acc_rows.restype = ctypes.c_int64
+        L.ens_size.argtypes = [vp]
+        L.ens_size.restype = ctypes.c_int64
+        L.ens_dim.argtypes = [vp]
+        L.ens_dim.restype = ctypes.c_int32
+        L.ens_npar.argtypes = [vp]
+        L.ens_npar.restype = ctypes.c_int32
+        L.ens_autotune.argtypes = [vp, vp, ctypes.POINTER(EnsLaunch)]
+        L.ens_autotune.restype = st
+        L.ens_last_error.argtypes = [vp]
+        L.ens_last_error.restype = ctypes.c_char_p
+        L.ens_destroy.argtypes = [vp]
+        L.ens_destroy.restype = None
+        L.ens_km_coefficients.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp, vp,
+                                          ctypes.POINTER(EnsLiquid), vp, vp]
+        L.ens_km_coefficients.restype = st
+        L.ens_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _ptr(x, keep: list):
+    """Raw address of a float64 / int array (numpy or torch, host or device)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):                  # torch tensor
+        if not x.is_contiguous():
+            x = x.contiguous()
+        keep.append(x)
+        return x.data_ptr()
+    a = np.ascontiguousarray(x)
+    keep.append(a)
+    return a.ctypes.data
+
+
+def _as_f64(x):
+    if hasattr(x, "data_ptr"):
+        import torch
+        return x.to(torch.float64).contiguous()
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+def _check(status: int, ctx=None):
+    if status != ENS_OK:
+        msg = lib().ens_last_error(ctx).decode(errors="replace")
+        raise EnsError(status, msg)
+
+
+def make_tol(rtol=1e-10, atol=1e-10, dt0=1e-2, dt_min=1e-14, dt_max=1e-1, event_tol=1e-6,
+             max_steps=2_000_000_000, n_steps=0, n_phases=0, prec=ENS_FP64, phase_len=1.0,
+             acc_t_start=0.0, timeout_s=600.0) -> EnsTol:
+    return EnsTol(rtol, atol, dt0, dt_min, dt_max, event_tol, int(max_steps), int(n_steps),
+                  int(n_phases), int(prec), phase_len, acc_t_start, timeout_s)
+
+
+def make_launch(mode=ENS_LAUNCH_PERSISTENT, block=128, blocks_per_sm=2, use_graph=0,
+                cost_order=0) -> EnsLaunch:
+    return EnsLaunch(mode, block, blocks_per_sm, use_graph, cost_order)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+# ---------------------------------------------------------------------------
+
+def ens_version() -> str:
+    return lib().ens_version().decode()
+
+
+def ens_create(sys: int, n: int, params, y0, t_span, solver: int, tol: EnsTol) -> int:
+    """Returns the context handle (an int); inputs are copied by the library."""
+    keep = []
+    params = _as_f64(params)
+    y0 = _as_f64(y0)
+    ctx = ctypes.c_void_p()
+    ts = (ctypes.c_double * 2)(float(t_span[0]), float(t_span[1]))
+    st = lib().ens_create(ctypes.byref(ctx), int(sys), int(n), _ptr(params, keep), _ptr(y0, keep),
+                          ts, int(solver), ctypes.byref(tol))
+    _check(st, None)
+    return ctx.value
+
+
+def ens_set_inputs(ctx: int, params=None, y0=None, stream=None):
+    keep = []
+    params = None if params is None else _as_f64(params)
+    y0 = None if y0 is None else _as_f64(y0)
+    _check(lib().ens_set_inputs(ctx, _ptr(params, keep), _ptr(y0, keep), _stream(stream)), ctx)
+
+
+def ens_set_launch(ctx: int, cfg: EnsLaunch | None):
+    _check(lib().ens_set_launch(ctx, ctypes.byref(cfg) if cfg is not None else None), ctx)
+
+
+def ens_get_launch(ctx: int) -> EnsLaunch:
+    cfg = EnsLaunch()
+    _check(lib().ens_get_launch(ctx, ctypes.byref(cfg)), ctx)
+    return cfg
+
+
+def ens_solve(ctx: int, stream=None):
+    _check(lib().ens_solve(ctx, _stream(stream)), ctx)
+
+
+def ens_sync(ctx: int, raise_on_system: bool = False) -> int:
+    """Wait for the last solve; returns ENS_OK / ENS_ETIMEOUT / ENS_ESYSTEM
+    (raises for call failures, and for the latter two if asked)."""
+    st = lib().ens_sync(ctx)
+    if st in (ENS_ETIMEOUT, ENS_ESYSTEM) and not raise_on_system:
+        return st
+    _check(st, ctx)
+    return st
+
+
+_READ_DTYPE = {ENS_STATE: np.float64, ENS_ACC: np.float64, ENS_STATUS: np.int32,
+               ENS_NSTEPS: np.int64, ENS_NREJ: np.int64, ENS_NRHS: np.int64,
+               ENS_TIME: np.float64, ENS_DT: np.float64}
+
+
+def ens_read(ctx: int, which: int, dst=None):
+    """Copy one output into dst (numpy / torch, host or device); with dst=None
+    a numpy array of the selector's shape is returned."""
+    L = lib()
+    n = L.ens_size(ctx)
+    if dst is None:
+        rows = {ENS_STATE: L.ens_dim(ctx), ENS_ACC: L.ens_acc_rows(ctx)}.get(which, 1)
+        dst = np.empty((rows, n) if which in (ENS_STATE, ENS_ACC) else (n,), dtype=_READ_DTYPE[which])
+    keep = []
+    p = _ptr(dst, keep)
+    nbytes = dst.element_size() * dst.numel() if hasattr(dst, "element_size") else dst.nbytes
+    _check(L.ens_read(ctx, int(which), p, nbytes), ctx)
+    return dst
+
+
+def ens_acc_rows(ctx: int) -> int:
+    return int(lib().ens_acc_rows(ctx))
+
+
+def ens_size(ctx: int) -> int:
+    return int(lib().ens_size(ctx))
+
+
+def ens_dim(ctx: int) -> int:
+    return int(lib().ens_dim(ctx))
+
+
+def ens_npar(ctx: int) -> int:
+    return int(lib().ens_npar(ctx))
+
+
+def ens_autotune(ctx: int, stream=None) -> EnsLaunch:
+    best = EnsLaunch()
+    _check(lib().ens_autotune(ctx, _stream(stream), ctypes.byref(best)), ctx)
+    return best
+
+
+def ens_last_error(ctx: int | None = None) -> str:
+    return lib().ens_last_error(ctx).decode(errors="replace")
+
+
+def ens_destroy(ctx: int):
+    if ctx:
+        lib().ens_destroy(ctx)
+
+
+def ens_km_coefficients(pA1, f1, pA2, f2, theta, RE, liquid: dict, out=None, stream=None):
+    """C0..C12 (13, n) from SI parameters; all arrays host (numpy) or all
+    device (torch CUDA tensors)."""
+    arrs = [_as_f64(a) for a in (pA1, f1, pA2, f2, theta, RE)]
+    n = int(arrs[0].numel() if hasattr(arrs[0], "numel") else arrs[0].size)
+    if out is None:
+        if hasattr(arrs[0], "data_ptr") and arrs[0].is_cuda:
+            import torch
+            out = torch.empty((13, n), dtype=torch.float64, device=arrs[0].device)
+        else:
+            out = np.empty((13, n), dtype=np.float64)
+    keep = []
+    liq = EnsLiquid(*[float(liquid[k]) for k in ("rho", "c", "mu", "sigma", "pv", "pinf", "gamma")])
+    st = lib().ens_km_coefficients(n, *[_ptr(a, keep) for a in arrs], ctypes.byref(liq),
+                                   _ptr(out, keep), _stream(stream))
+    _check(st, None)
+    return out

@@ -60,8 +60,10 @@ struct Rk4Args {
   const double* y0;      // [dim][n]
   double* y;             // [dim][n]
   double* t_out;         // [n]
+  double* dt_out;        // [n]
   int32_t* status;       // [n]
   int64_t* nacc;         // [n]
+  int64_t* nrej;         // [n]
   int64_t* nrhs;         // [n]
   Scratch* scratch;
   double t0, dt;
@@ -89,6 +91,12 @@ struct AdaptArgs {
   int32_t n_phases;
   int32_t persistent;
   uint64_t timeout_ns;
+};
+
+// Grid of an adaptive launch.
+struct AdaptLaunch {
+  int64_t grid;
+  int block;
 };
 
 // Nanosecond wall clock of the GPU (PTX %globaltimer).

@@ -1,0 +1,154 @@
+// rhs.cuh -- right-hand sides of the built-in systems as inlined device code.
+//
+// Each system is a struct with the state dimension, a parameter loader (from
+// the SoA parameter array into registers) and the RHS evaluation.  Two
+// arithmetic flavours exist for the fixed-step systems:
+//   - fast   : fused multiply-add wherever it shortens the FP64 pipe work;
+//   - strict : IEEE double with no contraction, operations in the order the
+//              paper writes the equation (bit-reproducible against a plain
+//              C evaluation of the same formula).
+#pragma once
+
+#include "common.cuh"
+
+namespace ens {
+
+// Double operations that the compiler may not fuse (strict flavour).
+__device__ __forceinline__ double sadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ssub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double smul(double a, double b) { return __dmul_rn(a, b); }
+
+// ---------------------------------------------------------------------------
+// x' = x^2 - p   (Sec. 3, Eq. exemplary_system)
+// ---------------------------------------------------------------------------
+struct X2P {
+  static constexpr int kDim = 1;
+  static constexpr int kPar = 1;
+  double p;
+  __device__ __forceinline__ void load(const double* P, int64_t n, int64_t i) { p = P[i]; }
+  template <bool STRICT>
+  __device__ __forceinline__ void f(double t, const double* y, double* dy) const {
+    (void)t;
+    if (STRICT) dy[0] = ssub(smul(y[0], y[0]), p);
+    else dy[0] = fma(y[0], y[0], -p);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Lorenz (Sec. 4.1, Eqs. Lorenz1-3): x1' = sigma (x2 - x1),
+// x2' = rho x1 - x2 - x1 x3, x3' = x1 x2 - b x3.
+// ---------------------------------------------------------------------------
+struct Lorenz {
+  static constexpr int kDim = 3;
+  static constexpr int kPar = 3;
+  double rho, sigma, b;
+  __device__ __forceinline__ void load(const double* P, int64_t n, int64_t i) {
+    rho = P[i];
+    sigma = P[n + i];
+    b = P[2 * n + i];
+  }
+  template <bool STRICT>
+  __device__ __forceinline__ void f(double t, const double* y, double* dy) const {
+    (void)t;
+    if (STRICT) {
+      dy[0] = smul(sigma, ssub(y[1], y[0]));
+      dy[1] = ssub(ssub(smul(rho, y[0]), y[1]), smul(y[0], y[2]));
+      dy[2] = ssub(smul(y[0], y[1]), smul(b, y[2]));
+    } else {
+      dy[0] = sigma * (y[1] - y[0]);
+      dy[1] = fma(-y[0], y[2], fma(rho, y[0], -y[1]));
+      dy[2] = fma(y[0], y[1], -b * y[2]);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Dimensionless Keller-Miksis (Sec. 4.2, Eqs. dimensionless_system1-2,
+// numerator, denominator):
+//   y1' = y2,   y2' = N_KM / D_KM,
+//   N_KM = (C0 + C1 y2) (1/y1)^C10 - C2 (1 + C9 y2) - C3/y1 - C4 y2/y1
+//          - (1 - C9 y2 / 3) (3/2) y2^2
+//          - (C5 sin 2 pi tau + C6 sin(2 pi C11 tau + C12)) (1 + C9 y2)
+//          - y1 (C7 cos 2 pi tau + C8 cos(2 pi C11 tau + C12)),
+//   D_KM = y1 - C9 y1 y2 + C4 C9.
+// Following the paper's cost notes (Sec. 3.3): one reciprocal of y1 is
+// shared by the three 1/y1 terms, sine and cosine of one angle come from one
+// sincospi call, and the angle 2 pi tau is passed as 2 tau in units of pi.
+// DUAL selects the second driving frequency (C6, C8 != 0).
+// ---------------------------------------------------------------------------
+template <bool DUAL>
+struct KellerMiksis {
+  static constexpr int kDim = 2;
+  static constexpr int kPar = 13;
+  double C0, C1, C2, C3, C4, C5, C6, C7, C8, C9, C10, C11, C12pi, C4C9;
+  __device__ __forceinline__ void load(const double* P, int64_t n, int64_t i) {
+    C0 = P[i];
+    C1 = P[n + i];
+    C2 = P[2 * n + i];
+    C3 = P[3 * n + i];
+    C4 = P[4 * n + i];
+    C5 = P[5 * n + i];
+    C6 = P[6 * n + i];
+    C7 = P[7 * n + i];
+    C8 = P[8 * n + i];
+    C9 = P[9 * n + i];
+    C10 = P[10 * n + i];
+    C11 = P[11 * n + i];
+    C12pi = P[12 * n + i] * (1.0 / 3.141592653589793238462643383279502884);
+    C4C9 = C4 * C9;
+  }
+  __device__ __forceinline__ void f(double tau, const double* y, double* dy) const {
+    const double y1 = y[0], y2 = y[1];
+    const double rx = 1.0 / y1;
+    const double g = pow(rx, C10);
+    double s1, c1;
+    sincospi(2.0 * tau, &s1, &c1);
+    const double one_c9y2 = fma(C9, y2, 1.0);
+    double forc_s = C5 * s1;
+    double forc_c = C7 * c1;
+    if (DUAL) {
+      double s2, c2;
+      sincospi(fma(2.0 * C11, tau, C12pi), &s2, &c2);
+      forc_s = fma(C6, s2, forc_s);
+      forc_c = fma(C8, c2, forc_c);
+    }
+    // (1 - C9 y2 / 3) * 1.5 * y2^2 = (1.5 - 0.5 C9 y2) y2^2
+    const double kin = fma(-0.5 * C9, y2, 1.5) * (y2 * y2);
+    double N = fma(C1, y2, C0) * g;
+    N = fma(-C2, one_c9y2, N);
+    N = fma(-fma(C4, y2, C3), rx, N);
+    N -= kin;
+    N = fma(-forc_s, one_c9y2, N);
+    N = fma(-y1, forc_c, N);
+    const double D = fma(-C9 * y1, y2, y1) + C4C9;
+    dy[0] = y2;
+    dy[1] = N / D;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Pressure relief valve (Sec. 4.3, Eqs. pressure_relief_valve_1-3):
+//   y1' = y2, y2' = -kappa y2 - (y1 + delta) + y3, y3' = beta (q - y1 sqrt(y3)).
+// sqrt is taken of max(y3, 0): y3 >= 0 for q > 0, the clamp only keeps a
+// rounding excursion from producing a NaN.
+// ---------------------------------------------------------------------------
+struct ReliefValve {
+  static constexpr int kDim = 3;
+  static constexpr int kPar = 5;
+  double q, kappa, delta, beta, r;
+  __device__ __forceinline__ void load(const double* P, int64_t n, int64_t i) {
+    q = P[i];
+    kappa = P[n + i];
+    delta = P[2 * n + i];
+    beta = P[3 * n + i];
+    r = P[4 * n + i];
+  }
+  __device__ __forceinline__ void f(double t, const double* y, double* dy) const {
+    (void)t;
+    dy[0] = y[1];
+    dy[1] = fma(-kappa, y[1], y[2] - (y[0] + delta));
+    dy[2] = beta * fma(-y[0], sqrt(fmax(y[2], 0.0)), q);
+  }
+};
+
+}  // namespace ens

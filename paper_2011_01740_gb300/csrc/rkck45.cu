@@ -1,0 +1,528 @@
+// rkck45.cu -- adaptive Cash-Karp 4(5) ensemble kernels.
+//
+// One lane integrates one system at a time with state, the six stage
+// derivatives and the parameters in registers.  Every loop iteration of a lane
+// is exactly one trial step, so all lanes of a warp run the same instruction
+// stream (the six right-hand-side evaluations) whatever their system's time,
+// step size or phase; only the short accept / reject / event / phase-end
+// branches diverge (Sec. 3.2.1 on divergence; Sec. 4.2 on asynchronous time
+// stepping).
+//
+// Two launch modes:
+//   plain       : system = global thread index; the lane retires when its
+//                 system is done.
+//   persistent  : a fixed grid of lanes; a lane that finishes its system
+//                 claims the next one with atomicAdd on a device counter
+//                 (work stealing), so uneven step counts do not leave warps
+//                 idle.  An optional claim order lets the host schedule the
+//                 longest systems first.
+//
+// Step-size control (the paper gives only the tolerances, Sec. 4.2.1):
+//   sc_i = atol + rtol max(|y_i|, |y5_i|),  E = max_i |err_i| / sc_i,
+//   accept iff E <= 1, fac = clamp(0.9 E^(-1/5), 0.2, 5) (5 if E = 0, 0.2 if
+//   E is not a number), new step h fac bounded by [dt_min, dt_max]; a step
+//   shortened to land on a phase end or an event keeps the previous proposal.
+// Loops are bounded: max_steps trials per system, 40 event retries in a row,
+// and a wall-clock budget read from %globaltimer; there are no spin-waits.
+#include "common.cuh"
+#include "rhs.cuh"
+
+namespace ens {
+
+// ---------------------------------------------------------------------------
+// one Cash-Karp trial: stages 2..6 from k1, fifth-order solution and error
+// ---------------------------------------------------------------------------
+template <class Sys>
+__device__ __forceinline__ void ck_trial(const Sys& s, double t, double h, const double* y,
+                                         const double* k1, double* y5, double* err) {
+  constexpr int D = Sys::kDim;
+  double k2[D], k3[D], k4[D], k5[D], k6[D], ys[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) ys[c] = fma(h, ck::a21 * k1[c], y[c]);
+  s.f(fma(ck::c2, h, t), ys, k2);
+#pragma unroll
+  for (int c = 0; c < D; ++c) ys[c] = fma(h, fma(ck::a32, k2[c], ck::a31 * k1[c]), y[c]);
+  s.f(fma(ck::c3, h, t), ys, k3);
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+    ys[c] = fma(h, fma(ck::a43, k3[c], fma(ck::a42, k2[c], ck::a41 * k1[c])), y[c]);
+  s.f(fma(ck::c4, h, t), ys, k4);
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+    ys[c] = fma(h, fma(ck::a54, k4[c], fma(ck::a53, k3[c], fma(ck::a52, k2[c], ck::a51 * k1[c]))),
+                y[c]);
+  s.f(t + h, ys, k5);  // c5 = 1
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+    ys[c] = fma(h,
+                fma(ck::a65, k5[c],
+                    fma(ck::a64, k4[c], fma(ck::a63, k3[c], fma(ck::a62, k2[c], ck::a61 * k1[c])))),
+                y[c]);
+  s.f(fma(ck::c6, h, t), ys, k6);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    y5[c] = fma(h, fma(ck::b6, k6[c], fma(ck::b4, k4[c], fma(ck::b3, k3[c], ck::b1 * k1[c]))), y[c]);
+    err[c] = h * fma(ck::d6, k6[c],
+                     fma(ck::d5, k5[c], fma(ck::d4, k4[c], fma(ck::d3, k3[c], ck::d1 * k1[c]))));
+  }
+}
+
+template <int D>
+__device__ __forceinline__ double err_norm(const double* y, const double* y5, const double* err,
+                                           double rtol, double atol) {
+  double E = 0.0;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const double sc = fma(rtol, fmax(fabs(y[c]), fabs(y5[c])), atol);
+    const double r = fabs(err[c]) / sc;
+    if (isnan(r)) E = r;
+    else if (r > E) E = r;   // E stays NaN once NaN: NaN > r comparisons are false
+  }
+  return E;
+}
+
+__device__ __forceinline__ double step_factor(double E) {
+  if (isnan(E)) return 0.2;
+  if (E == 0.0) return 5.0;
+  double fac = 0.9 * pow(E, -0.2);
+  fac = fac < 0.2 ? 0.2 : fac;
+  fac = fac > 5.0 ? 5.0 : fac;
+  return fac;
+}
+
+// Claim the next system of a persistent lane (or the lane's own system in
+// plain mode).  Returns -1 when no work is left.
+__device__ __forceinline__ int64_t claim(const AdaptArgs& a, bool first) {
+  if (!a.persistent) {
+    if (!first) return -1;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    return i < a.n ? i : -1;
+  }
+  const unsigned long long k = atomicAdd(&a.scratch->next, 1ULL);
+  if (k >= (unsigned long long)a.n) return -1;
+  return a.order ? (int64_t)a.order[k] : (int64_t)k;
+}
+
+// ---------------------------------------------------------------------------
+// Phase mode (Keller-Miksis, Sec. 4.2): n_phases integrations over
+// tau in [t0, t0 + phase_len] with tau reset at each phase start; running max
+// and min of y1 over the accepted step points and the phase start.
+// ---------------------------------------------------------------------------
+template <class Sys>
+__global__ void __launch_bounds__(128) ck_phased_kernel(AdaptArgs a) {
+  constexpr int D = Sys::kDim;
+  const double tau_end = a.t0 + a.phase_len;
+  const uint64_t deadline = global_ns() + a.timeout_ns;
+  int64_t i = claim(a, true);
+  bool timed_out = false;
+  Sys s;
+  double y[D], k1[D], y5[D], err[D];
+  double tau = a.t0, dt = a.dt0, ymax = 0.0, ymin = 0.0;
+  int32_t ph = 0, st = 0;
+  uint32_t trials = 0, nacc = 0, nrej = 0, nrhs = 0, iter = 0;
+  bool k1v = false;
+
+  auto start_system = [&](int64_t sys) {
+    s.load(a.params, a.n, sys);
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = a.y0[c * a.n + sys];
+    tau = a.t0;
+    dt = a.dt0;
+    ph = 0;
+    st = timed_out ? kStTimeout : 0;
+    trials = nacc = nrej = nrhs = 0;
+    k1v = false;
+    ymax = ymin = y[0];
+  };
+  auto finish_system = [&](int64_t sys) {
+    // phases that were not completed are marked NaN
+    for (int p = ph; p < a.n_phases; ++p) {
+      a.acc[(int64_t)(2 * p) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
+      a.acc[(int64_t)(2 * p + 1) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) a.y[c * a.n + sys] = y[c];
+    a.t_out[sys] = tau;
+    a.dt_out[sys] = dt;
+    a.status[sys] = st;
+    a.nacc[sys] = nacc;
+    a.nrej[sys] = nrej;
+    a.nrhs[sys] = nrhs;
+    if (st) atomicOr(&a.scratch->any_status, (unsigned)st);
+  };
+
+  if (i >= 0) start_system(i);
+  while (i >= 0) {
+    bool sys_done = false;
+    if (st == 0) {
+      if ((++iter & 127u) == 0 && global_ns() > deadline) timed_out = true;
+      if (timed_out) {
+        st |= kStTimeout;
+      } else if (trials >= (uint64_t)a.max_steps) {
+        st |= kStMaxSteps;
+      }
+    }
+    if (st != 0) {
+      // close the current phase with what it has, then retire the system
+      if (ph < a.n_phases) {
+        a.acc[(int64_t)(2 * ph) * a.n + i] = ymax;
+        a.acc[(int64_t)(2 * ph + 1) * a.n + i] = ymin;
+        ++ph;
+      }
+      sys_done = true;
+    } else {
+      double h = dt;
+      bool clamped = false;
+      if (h >= tau_end - tau) {
+        h = tau_end - tau;
+        clamped = true;
+      }
+      if (!k1v) {
+        s.f(tau, y, k1);
+        ++nrhs;
+        k1v = true;
+      }
+      ck_trial(s, tau, h, y, k1, y5, err);
+      nrhs += 5;
+      ++trials;
+      const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
+      const double fac = step_factor(E);
+      if (E <= 1.0) {
+        tau = clamped ? tau_end : tau + h;
+#pragma unroll
+        for (int c = 0; c < D; ++c) y[c] = y5[c];
+        k1v = false;
+        ++nacc;
+        ymax = fmax(ymax, y[0]);
+        ymin = fmin(ymin, y[0]);
+        if (!clamped) {
+          dt = h * fac;
+          dt = dt > a.dt_max ? a.dt_max : dt;
+          dt = dt < a.dt_min ? a.dt_min : dt;
+        }
+        if (!(tau < tau_end)) {
+          a.acc[(int64_t)(2 * ph) * a.n + i] = ymax;
+          a.acc[(int64_t)(2 * ph + 1) * a.n + i] = ymin;
+          ++ph;
+          if (ph >= a.n_phases) {
+            sys_done = true;
+          } else {
+            tau = a.t0;
+            ymax = ymin = y[0];
+          }
+        }
+      } else {
+        ++nrej;
+        dt = h * fac;
+        if (dt < a.dt_min) st |= kStDtUnderflow;  // retired at the next iteration
+      }
+    }
+    if (sys_done) {
+      finish_system(i);
+      i = claim(a, false);
+      if (i >= 0) start_system(i);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Event mode (pressure relief valve, Sec. 4.3).  Events g1 = y1 (impact,
+// body reaching the seat while moving towards it) and g2 = y2 (local maximum
+// of y1, the Poincare section), both falling, absolute tolerance event_tol:
+//   - after a trial that passes the error test, the impact overshoots when
+//     y1(t+h) < -tol, the maximum when y2(t) > tol and y2(t+h) < -tol; the
+//     trial is redone with the step cut by the secant fraction g(t) /
+//     (g(t) - g(t+h)) of the earliest overshooting event (one half when the
+//     impact starts inside the band |y1| <= tol);
+//   - otherwise the step is accepted; at its end the maximum is located when
+//     y2(t) > tol and |y2| <= tol (y1 goes to the ring of Poincare points), the
+//     impact when |y1| <= tol and y2 < 0 (y1 <- 0, y2 <- -r y2, Eqs.
+//     impact_law_1-3);
+//   - a bounce whose apex would stay inside the band (v^2 <= 2 a tol with
+//     a = delta - y3 > 0 pressing the body onto the seat) leaves the body on
+//     the seat: y1 = y2 = 0 while y3 rises as beta q until y3 = delta, an
+//     interval advanced in closed form.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) ck_events_kernel(AdaptArgs a) {
+  using Sys = ReliefValve;
+  constexpr int D = Sys::kDim;
+  const uint64_t deadline = global_ns() + a.timeout_ns;
+  const double etol = a.event_tol;
+  int64_t i = claim(a, true);
+  bool timed_out = false;
+  Sys s;
+  double y[D], k1[D], y5[D], err[D];
+  double t = a.t0, dt = a.dt0, h_ev = 0.0, ymin = 0.0;
+  int32_t st = 0, ev_retries = 0;
+  uint32_t trials = 0, nacc = 0, nrej = 0, nrhs = 0, nmax = 0, nimp = 0, iter = 0;
+  bool k1v = false, stuck = false;
+
+  auto start_system = [&](int64_t sys) {
+    s.load(a.params, a.n, sys);
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = a.y0[c * a.n + sys];
+    t = a.t0;
+    dt = a.dt0;
+    h_ev = 0.0;
+    st = timed_out ? kStTimeout : 0;
+    ev_retries = 0;
+    trials = nacc = nrej = nrhs = nmax = nimp = 0;
+    k1v = false;
+    stuck = false;
+    ymin = (t >= a.acc_t_start) ? y[0] : __longlong_as_double(0x7ff0000000000000LL);
+    for (int r = 0; r < kRing; ++r)
+      a.acc[(int64_t)r * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
+  };
+  auto finish_system = [&](int64_t sys) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) a.y[c * a.n + sys] = y[c];
+    a.acc[(int64_t)kRing * a.n + sys] = ymin;
+    a.acc[(int64_t)(kRing + 1) * a.n + sys] = (double)nmax;
+    a.acc[(int64_t)(kRing + 2) * a.n + sys] = (double)nimp;
+    a.t_out[sys] = t;
+    a.dt_out[sys] = dt;
+    a.status[sys] = st;
+    a.nacc[sys] = nacc;
+    a.nrej[sys] = nrej;
+    a.nrhs[sys] = nrhs;
+    if (st) atomicOr(&a.scratch->any_status, (unsigned)st);
+  };
+
+  if (i >= 0) start_system(i);
+  while (i >= 0) {
+    bool sys_done = false;
+    if (st == 0) {
+      if ((++iter & 127u) == 0 && global_ns() > deadline) timed_out = true;
+      if (timed_out) st |= kStTimeout;
+      else if (!stuck && trials >= (uint64_t)a.max_steps) st |= kStMaxSteps;
+    }
+    if (st != 0) {
+      sys_done = true;
+    } else if (stuck) {
+      // closed-form interval on the seat: y1 = y2 = 0, y3' = beta q
+      const double t_lift = t + (s.delta - y[2]) / (s.beta * s.q);
+      if (t_lift >= a.t1) {
+        y[2] = y[2] + s.beta * s.q * (a.t1 - t);
+        t = a.t1;
+      } else {
+        y[2] = s.delta;
+        t = t_lift;
+        stuck = false;
+      }
+      k1v = false;
+      if (t >= a.acc_t_start && y[0] < ymin) ymin = y[0];
+      if (!(t < a.t1)) sys_done = true;
+    } else {
+      double h = dt;
+      int limited = 0;
+      if (h >= a.t1 - t) {
+        h = a.t1 - t;
+        limited = 1;
+      }
+      if (h_ev > 0.0 && h_ev < h) {
+        h = h_ev;
+        limited = 2;
+      }
+      if (!k1v) {
+        s.f(t, y, k1);
+        ++nrhs;
+        k1v = true;
+      }
+      ck_trial(s, t, h, y, k1, y5, err);
+      nrhs += 5;
+      ++trials;
+      const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
+      const double fac = step_factor(E);
+      if (!(E <= 1.0)) {
+        ++nrej;
+        dt = h * fac;
+        h_ev = 0.0;
+        if (dt < a.dt_min) st |= kStDtUnderflow;
+      } else {
+        double best = 2.0;
+        bool overshoot = false;
+        if (y5[0] < -etol) {  // impact beyond the band
+          const double frac = (y[0] > etol) ? y[0] / (y[0] - y5[0]) : 0.5;
+          best = frac < best ? frac : best;
+          overshoot = true;
+        }
+        if (y[1] > etol && y5[1] < -etol) {  // maximum beyond the band
+          const double frac = y[1] / (y[1] - y5[1]);
+          best = frac < best ? frac : best;
+          overshoot = true;
+        }
+        if (overshoot) {
+          if (++ev_retries > kEventRetries) st |= kStEventNoConverge;
+          else h_ev = h * best;
+        } else {
+          const double y1_old = y[1];
+#pragma unroll
+          for (int c = 0; c < D; ++c) y[c] = y5[c];
+          t = (limited == 1) ? a.t1 : t + h;
+          k1v = false;
+          ++nacc;
+          ev_retries = 0;
+          h_ev = 0.0;
+          if (!limited) {
+            dt = h * fac;
+            dt = dt > a.dt_max ? a.dt_max : dt;
+            dt = dt < a.dt_min ? a.dt_min : dt;
+          }
+          if (y1_old > etol && fabs(y[1]) <= etol) {  // Poincare point
+            a.acc[(int64_t)(nmax % kRing) * a.n + i] = y[0];
+            ++nmax;
+          }
+          if (fabs(y[0]) <= etol && y[1] < 0.0) {  // impact law
+            y[0] = 0.0;
+            y[1] = -s.r * y[1];
+            ++nimp;
+            const double push = s.delta - y[2];
+            if (push > 0.0 && y[1] * y[1] <= 2.0 * push * etol) {
+              y[1] = 0.0;
+              stuck = true;
+            }
+          }
+          if (t >= a.acc_t_start && y[0] < ymin) ymin = y[0];
+          if (!(t < a.t1)) sys_done = true;
+        }
+      }
+    }
+    if (sys_done) {
+      finish_system(i);
+      i = claim(a, false);
+      if (i >= 0) start_system(i);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// plain adaptive integration over [t0, t1] (no phases, no events)
+// ---------------------------------------------------------------------------
+template <class Sys>
+__global__ void __launch_bounds__(128) ck_plain_kernel(AdaptArgs a) {
+  constexpr int D = Sys::kDim;
+  const uint64_t deadline = global_ns() + a.timeout_ns;
+  int64_t i = claim(a, true);
+  bool timed_out = false;
+  Sys s;
+  double y[D], k1[D], y5[D], err[D];
+  double t = a.t0, dt = a.dt0;
+  int32_t st = 0;
+  uint32_t trials = 0, nacc = 0, nrej = 0, nrhs = 0, iter = 0;
+  bool k1v = false;
+  auto start_system = [&](int64_t sys) {
+    s.load(a.params, a.n, sys);
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = a.y0[c * a.n + sys];
+    t = a.t0;
+    dt = a.dt0;
+    st = timed_out ? kStTimeout : 0;
+    trials = nacc = nrej = nrhs = 0;
+    k1v = false;
+  };
+  auto finish_system = [&](int64_t sys) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) a.y[c * a.n + sys] = y[c];
+    a.t_out[sys] = t;
+    a.dt_out[sys] = dt;
+    a.status[sys] = st;
+    a.nacc[sys] = nacc;
+    a.nrej[sys] = nrej;
+    a.nrhs[sys] = nrhs;
+    if (st) atomicOr(&a.scratch->any_status, (unsigned)st);
+  };
+  if (i >= 0) start_system(i);
+  while (i >= 0) {
+    bool sys_done = false;
+    if (st == 0) {
+      if ((++iter & 127u) == 0 && global_ns() > deadline) timed_out = true;
+      if (timed_out) st |= kStTimeout;
+      else if (trials >= (uint64_t)a.max_steps) st |= kStMaxSteps;
+    }
+    if (st != 0) {
+      sys_done = true;
+    } else {
+      double h = dt;
+      bool clamped = false;
+      if (h >= a.t1 - t) {
+        h = a.t1 - t;
+        clamped = true;
+      }
+      if (!k1v) {
+        s.f(t, y, k1);
+        ++nrhs;
+        k1v = true;
+      }
+      ck_trial(s, t, h, y, k1, y5, err);
+      nrhs += 5;
+      ++trials;
+      const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
+      const double fac = step_factor(E);
+      if (E <= 1.0) {
+        t = clamped ? a.t1 : t + h;
+#pragma unroll
+        for (int c = 0; c < D; ++c) y[c] = y5[c];
+        k1v = false;
+        ++nacc;
+        if (!clamped) {
+          dt = h * fac;
+          dt = dt > a.dt_max ? a.dt_max : dt;
+          dt = dt < a.dt_min ? a.dt_min : dt;
+        }
+        if (!(t < a.t1)) sys_done = true;
+      } else {
+        ++nrej;
+        dt = h * fac;
+        if (dt < a.dt_min) st |= kStDtUnderflow;
+      }
+    }
+    if (sys_done) {
+      finish_system(i);
+      i = claim(a, false);
+      if (i >= 0) start_system(i);
+    }
+  }
+}
+
+// Adapter so that fixed-step systems can run through the adaptive kernels.
+template <class Fixed>
+struct AdaptFixed : Fixed {
+  __device__ __forceinline__ void f(double t, const double* y, double* dy) const {
+    Fixed::template f<false>(t, y, dy);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_ck45(int sys, bool dual, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  if (L.grid <= 0 || L.grid > 0x7fffffffLL || L.block <= 0) return cudaErrorInvalidConfiguration;
+  const dim3 g((unsigned)L.grid), b((unsigned)L.block);
+  if (a.n_phases > 0) {
+    switch (sys) {
+      case ENS_SYS_KELLER_MIKSIS:
+        if (dual) ck_phased_kernel<KellerMiksis<true>><<<g, b, 0, s>>>(a);
+        else ck_phased_kernel<KellerMiksis<false>><<<g, b, 0, s>>>(a);
+        break;
+      case ENS_SYS_LORENZ: ck_phased_kernel<AdaptFixed<Lorenz>><<<g, b, 0, s>>>(a); break;
+      case ENS_SYS_TOY_X2P: ck_phased_kernel<AdaptFixed<X2P>><<<g, b, 0, s>>>(a); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else if (sys == ENS_SYS_RELIEF_VALVE) {
+    ck_events_kernel<<<g, b, 0, s>>>(a);
+  } else {
+    switch (sys) {
+      case ENS_SYS_KELLER_MIKSIS:
+        if (dual) ck_plain_kernel<KellerMiksis<true>><<<g, b, 0, s>>>(a);
+        else ck_plain_kernel<KellerMiksis<false>><<<g, b, 0, s>>>(a);
+        break;
+      case ENS_SYS_LORENZ: ck_plain_kernel<AdaptFixed<Lorenz>><<<g, b, 0, s>>>(a); break;
+      case ENS_SYS_TOY_X2P: ck_plain_kernel<AdaptFixed<X2P>><<<g, b, 0, s>>>(a); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ens

@@ -1,0 +1,85 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+entry point of include/ens.h; argument validation fails cleanly; the host
+planner (Keller-Miksis coefficients) agrees with the oracle's own derivation."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "ens.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(ens_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def ens():
+    import paper_2011_01740_gb300 as ens
+    ens.lib()
+    return ens
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ("ens_create", "ens_solve", "ens_sync", "ens_read", "ens_last_error", "ens_destroy",
+                 "ens_set_inputs", "ens_set_launch", "ens_autotune", "ens_km_coefficients"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(ens):
+    L = ens.lib()
+    missing = [n for n in _declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    assert "sm_103a" in ens.ens_version()
+
+
+def test_python_binding_has_the_same_names(ens):
+    for n in _declared_functions():
+        assert hasattr(ens, n), n
+
+
+def test_create_rejects_bad_arguments_without_touching_a_device(ens):
+    tol = ens.make_tol(dt0=0.01, n_steps=10)
+    with pytest.raises(ens.EnsError) as e:
+        ens.ens_create(ens.ENS_SYS_LORENZ, -1, np.zeros((3, 1)), np.zeros((3, 1)), (0, 0), ens.ENS_RK4, tol)
+    assert e.value.status == ens.ENS_EINVAL
+    with pytest.raises(ens.EnsError) as e:
+        ens.ens_create(7, 1, np.zeros((3, 1)), np.zeros((3, 1)), (0, 0), ens.ENS_RK4, tol)
+    assert e.value.status == ens.ENS_EINVAL
+    with pytest.raises(ens.EnsError) as e:   # RK4 cannot run the impacting valve
+        ens.ens_create(ens.ENS_SYS_RELIEF_VALVE, 1, np.zeros((5, 1)), np.zeros((3, 1)), (0, 1),
+                       ens.ENS_RK4, tol)
+    assert e.value.status == ens.ENS_ENOTSUP
+    bad = ens.make_tol(rtol=-1.0)
+    with pytest.raises(ens.EnsError) as e:
+        ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, 1, np.zeros((13, 1)), np.zeros((2, 1)), (0, 1),
+                       ens.ENS_RKCK45, bad)
+    assert e.value.status == ens.ENS_EINVAL
+    assert "rtol" in ens.ens_last_error(None)
+
+
+def test_null_context_calls_are_harmless(ens):
+    L = ens.lib()
+    assert L.ens_solve(None, None) == ens.ENS_EINVAL
+    assert L.ens_sync(None) == ens.ENS_EINVAL
+    assert L.ens_acc_rows(None) == 0
+    L.ens_destroy(None)
+
+
+def test_host_planner_matches_oracle_coefficients(ens):
+    import oracle
+    from paper_2011_01740_gb300 import workloads as W
+    rng = np.random.default_rng(5)
+    n = 500
+    pA1, pA2 = rng.uniform(0, 2e5, n), rng.uniform(0, 1e5, n)
+    f1, f2 = rng.uniform(2e4, 1e6, n), rng.uniform(0, 2e6, n)
+    th, RE = rng.uniform(0, 6.28, n), rng.uniform(1e-6, 1e-4, n)
+    C = ens.ens_km_coefficients(pA1, f1, pA2, f2, th, RE, W.WATER_25C)
+    Co = oracle.km_coefficients(pA1, f1, pA2, f2, th, RE, oracle.liquid(**W.WATER_25C))
+    np.testing.assert_allclose(C, Co, rtol=4e-15, atol=0)

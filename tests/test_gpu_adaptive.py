@@ -1,0 +1,248 @@
+"""GPU parity of the adaptive Cash-Karp path: Keller-Miksis phase mode
+(Sec. 4.2) and the pressure relief valve with events (Sec. 4.3), through the
+C ABI, against the CPU oracle.
+
+Adaptive runs amplify rounding differences through the step sequence (an
+accept / reject decision that flips moves every later step point, and the
+per-period maximum is sampled at step points).  The comparison therefore
+runs on the well-conditioned systems, those whose oracle accessories move by
+less than 1e-9 when the initial state is perturbed by 1e-14 relative; there
+the GPU must match to 1e-8 relative.  The excluded fraction is bounded.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2011_01740_gb300 as ens
+from paper_2011_01740_gb300 import workloads as W
+from gpu_helpers import (ens_tol_from, km_coeffs_lib, km_coeffs_oracle, oracle_tol_from, rel_err,
+                         solve_gpu)
+
+pytestmark = pytest.mark.gpu
+
+ACC_TOL = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    ens.lib()
+
+
+def _well_conditioned(sys, params, y0, otol, delta=1e-14, rows=None):
+    a = oracle.cashkarp_solve(sys, params, y0, otol)
+    b = oracle.cashkarp_solve(sys, params, np.asarray(y0) * (1 + delta), otol)
+    sel = slice(None) if rows is None else rows
+    well = rel_err(b["acc"][sel], a["acc"][sel]) < 1e-9
+    well &= (a["status"] == 0) & (b["status"] == 0)
+    return a, well
+
+
+# ---------------------------------------------------------------------------
+# Keller-Miksis
+# ---------------------------------------------------------------------------
+
+def _km_gpu(km, launch=None, n_phases=None, **tolkw):
+    C = km_coeffs_lib(km["phys"], km["liquid"])
+    t = km["tol"]
+    tol = ens_tol_from(t, **({"n_phases": n_phases} if n_phases else {}), **tolkw)
+    return solve_gpu(ens.ENS_SYS_KELLER_MIKSIS, C, km["y0"], (t.t0, t.t1), ens.ENS_RKCK45, tol,
+                     launch=launch)
+
+
+def test_km_small_grid_parity():
+    km = W.km(19, 23, n_phases=4)          # 437 systems: 3 full blocks + a ragged tail
+    g = _km_gpu(km)
+    Co = km_coeffs_oracle(km["phys"], km["liquid"])
+    r, well = _well_conditioned(oracle.KM, Co, km["y0"], oracle_tol_from(km["tol"]))
+    assert g["sync"] == ens.ENS_OK and np.all(g["status"] == 0)
+    assert well.mean() > 0.9
+    err = rel_err(g["acc"], r["acc"])
+    assert np.all(err[well] < ACC_TOL), err[well].max()
+    assert np.all(rel_err(g["y"], r["y"])[well] < 1e-7)
+    # same step sequence on the well-conditioned systems
+    d = np.abs(g["nacc"] - r["nacc"]) / r["nacc"]
+    assert np.median(d[well]) == 0.0 and d[well].max() < 0.02
+    assert np.all(g["nrhs"] == 6 * (g["nacc"] + g["nrej"]) - g["nrej"])
+
+
+def test_km_full_grid_sampled_parity():
+    """131,044 systems (362 x 362 p_A x f grid), 64 periods, tol 1e-10: the
+    benchmarked launch, checked on a stratified sample of 192 systems."""
+    km = W.km()
+    g = _km_gpu(km)
+    n = km["y0"].shape[1]
+    assert g["sync"] == ens.ENS_OK and np.all(g["status"] == 0)
+    idx = W.subsample(n, 192)
+    sub = W.take(km, idx)
+    Co = km_coeffs_oracle(sub["phys"], sub["liquid"])
+    r, well = _well_conditioned(oracle.KM, Co, sub["y0"], oracle_tol_from(km["tol"]))
+    assert well.mean() > 0.75, well.mean()
+    err = rel_err(g["acc"][:, idx], r["acc"])
+    assert np.all(err[well] < ACC_TOL), (err[well].max(), idx[well][np.argmax(err[well])])
+    # every system: accessories are physical radii, finite and ordered
+    acc = g["acc"]
+    assert np.all(np.isfinite(acc)) and np.all(acc[0::2] >= acc[1::2]) and np.all(acc[1::2] > 0)
+    # the unforced row p_A = 0 stays at the equilibrium radius
+    assert np.abs(acc[:, :362] - 1.0).max() < 1e-8
+
+
+def test_km_launch_modes_and_graph_replay_are_bitwise_identical():
+    km = W.km(13, 29, n_phases=3)
+    ref = _km_gpu(km, launch=ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=64))
+    for L in (ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=128, blocks_per_sm=1),
+              ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=64, blocks_per_sm=4, use_graph=1),
+              ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=128, blocks_per_sm=2, cost_order=1)):
+        g = _km_gpu(km, launch=L)
+        for k in ("y", "acc", "nacc", "nrej", "nrhs", "status", "dt"):
+            assert np.array_equal(g[k], ref[k]), (k, L.as_dict())
+
+
+def test_km_graph_replays_and_set_inputs():
+    km = W.km(9, 11, n_phases=2)
+    C = km_coeffs_lib(km["phys"], km["liquid"])
+    tol = ens_tol_from(km["tol"])
+    n = C.shape[1]
+    ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, n, C, km["y0"], (0.0, 1.0), ens.ENS_RKCK45, tol)
+    try:
+        ens.ens_set_launch(ctx, ens.make_launch(use_graph=1))
+        outs = []
+        for _ in range(3):
+            ens.ens_solve(ctx)
+            assert ens.ens_sync(ctx) == ens.ENS_OK
+            outs.append(ens.ens_read(ctx, ens.ENS_ACC))
+        assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+        # new inputs through the same context (and graph)
+        y0b = km["y0"].copy()
+        y0b[0] = 1.05
+        ens.ens_set_inputs(ctx, None, y0b)
+        ens.ens_solve(ctx)
+        ens.ens_sync(ctx)
+        accb = ens.ens_read(ctx, ens.ENS_ACC)
+    finally:
+        ens.ens_destroy(ctx)
+    Co = km_coeffs_oracle(km["phys"], km["liquid"])
+    r = oracle.cashkarp_solve(oracle.KM, Co, y0b, oracle_tol_from(km["tol"]))
+    assert np.median(rel_err(accb, r["acc"])) < 1e-9
+
+
+def test_km_device_planner_matches_host_planner():
+    import torch
+    km = W.km(31, 37)
+    ph = km["phys"]
+    host = km_coeffs_lib(ph, km["liquid"])
+    dev = ens.ens_km_coefficients(*[torch.from_numpy(ph[k]).cuda() for k in
+                                    ("pA1", "f1", "pA2", "f2", "theta", "RE")], km["liquid"])
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(dev.cpu().numpy(), host, rtol=4e-16, atol=0)
+
+
+def test_km_dual_frequency_parity():
+    """Second driving component (P_A2, f2, theta != 0) with the omega2 form of C8."""
+    rng = np.random.default_rng(3)
+    n = 150
+    phys = dict(pA1=rng.uniform(0.2e5, 1.5e5, n), f1=rng.uniform(1e5, 8e5, n),
+                pA2=rng.uniform(0.1e5, 0.8e5, n), f2=rng.uniform(1e5, 1.5e6, n),
+                theta=rng.uniform(0, 6.28, n), RE=np.full(n, 10e-6))
+    km = dict(phys=phys, liquid=W.WATER_25C, y0=np.stack([np.ones(n), np.zeros(n)]),
+              tol=W.Tolerances(n_phases=3))
+    g = _km_gpu(km)
+    Co = km_coeffs_oracle(phys, W.WATER_25C)
+    r, well = _well_conditioned(oracle.KM, Co, km["y0"], oracle_tol_from(km["tol"]))
+    assert well.mean() > 0.8
+    assert np.all(rel_err(g["acc"], r["acc"])[well] < ACC_TOL)
+
+
+def test_km_status_words():
+    km = W.km(3, 4, n_phases=2)
+    g = _km_gpu(km, max_steps=5)
+    big = g["nacc"] + g["nrej"]
+    assert np.all((g["status"] & ens.ENS_SYS_MAX_STEPS) > 0)
+    assert np.all(big == 5)
+    assert np.all(np.isnan(g["acc"][2:]))           # phase 1 never completed
+    assert g["sync"] == ens.ENS_ESYSTEM
+    # an unreachable tolerance underflows the step size
+    g = _km_gpu(km, rtol=1e-30, atol=1e-30, dt_min=1e-6)
+    assert np.all((g["status"] & ens.ENS_SYS_DT_UNDERFLOW) > 0)
+    # the wall-clock budget stops the solve and is reported, not waited out
+    g = _km_gpu(W.km(20, 20, n_phases=64), timeout_s=1e-6)
+    assert np.all((g["status"] & ens.ENS_SYS_TIMEOUT) > 0)
+    assert g["sync"] == ens.ENS_ETIMEOUT
+
+
+# ---------------------------------------------------------------------------
+# pressure relief valve
+# ---------------------------------------------------------------------------
+
+def _prv(n, t1, q_min=0.2, q_max=10.0):
+    return W.prv(n, q_min=q_min, q_max=q_max, t1=t1)
+
+
+def _prv_gpu(wl, launch=None, **tolkw):
+    t = wl["tol"]
+    tol = ens_tol_from(t, **tolkw)
+    return solve_gpu(ens.ENS_SYS_RELIEF_VALVE, wl["params"], wl["y0"], (t.t0, t.t1), ens.ENS_RKCK45,
+                     tol, launch=launch)
+
+
+def _prv_compare(g, r, well, idx=None):
+    gi = (lambda a: a) if idx is None else (lambda a: a[..., idx])
+    acc = gi(g["acc"])
+    # counts of maxima and impacts agree exactly on the well-conditioned systems
+    assert np.array_equal(acc[33][well], r["acc"][33][well])
+    assert np.array_equal(acc[34][well], r["acc"][34][well])
+    err = rel_err(acc[:33], r["acc"][:33])
+    assert np.all(err[well] < ACC_TOL), err[well].max()
+    assert np.all(rel_err(gi(g["y"]), r["y"])[well] < 1e-7)
+
+
+def test_prv_small_parity():
+    wl = _prv(300, 64.0)
+    g = _prv_gpu(wl)
+    r, well = _well_conditioned(oracle.PRV, wl["params"], wl["y0"], oracle_tol_from(wl["tol"]))
+    assert g["sync"] == ens.ENS_OK and np.all(g["status"] == 0)
+    assert well.mean() > 0.75, well.mean()
+    _prv_compare(g, r, well)
+    assert np.all(g["t"] == 64.0)
+
+
+def test_prv_full_sweep_sampled_parity():
+    """262,144 valves, t in [0, 1024]: the benchmarked launch, on a sample."""
+    wl = _prv(262144, 1024.0)
+    g = _prv_gpu(wl)
+    assert g["sync"] == ens.ENS_OK and np.all(g["status"] == 0)
+    idx = W.subsample(262144, 96)
+    sub = W.take(wl, idx)
+    r, well = _well_conditioned(oracle.PRV, sub["params"], sub["y0"], oracle_tol_from(wl["tol"]))
+    assert well.mean() > 0.5, well.mean()
+    _prv_compare(g, r, well, idx)
+    # every valve: impacting below q ~ 7.5 (Sec. 4.3), pressure non-negative
+    q = wl["params"][0]
+    ymin = g["acc"][32]
+    assert np.mean(ymin[q < 7.0] == 0.0) > 0.95 and np.all(ymin[q > 8.0] > 0.0)
+    assert np.all(g["y"][2] >= 0.0)
+
+
+def test_prv_launch_modes_bitwise_identical():
+    wl = _prv(200, 32.0)
+    ref = _prv_gpu(wl, launch=ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=128))
+    g = _prv_gpu(wl, launch=ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=64, blocks_per_sm=1,
+                                            cost_order=1))
+    for k in ("y", "acc", "nacc", "nrej", "status"):
+        assert np.array_equal(g[k], ref[k]), k
+
+
+def test_autotune_returns_a_valid_launch():
+    km = W.km(16, 16, n_phases=2)
+    C = km_coeffs_lib(km["phys"], km["liquid"])
+    ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
+                         ens.ENS_RKCK45, ens_tol_from(km["tol"]))
+    try:
+        best = ens.ens_autotune(ctx)
+        assert best.mode in (ens.ENS_LAUNCH_PLAIN, ens.ENS_LAUNCH_PERSISTENT)
+        assert best.block % 32 == 0
+        ens.ens_solve(ctx)
+        assert ens.ens_sync(ctx) == ens.ENS_OK
+    finally:
+        ens.ens_destroy(ctx)

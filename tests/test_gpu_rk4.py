@@ -1,0 +1,119 @@
+"""GPU parity of the fixed-step RK4 path (Sec. 3 example, Sec. 4.1 Lorenz)
+against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2011_01740_gb300 as ens
+from paper_2011_01740_gb300 import workloads as W
+from gpu_helpers import rel_err, rk4_amplification, rk4_tolerance, solve_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    ens.lib()
+
+
+def _rk4(sys, wl, prec=ens.ENS_FP64, nsteps=None, launch=None):
+    nsteps = wl["nsteps"] if nsteps is None else nsteps
+    tol = ens.make_tol(dt0=wl["dt"], n_steps=nsteps, prec=prec)
+    return solve_gpu(sys, wl["params"], wl["y0"], (wl["t0"], 0.0), ens.ENS_RK4, tol, launch=launch)
+
+
+@pytest.mark.parametrize("n", [421, 16384])
+def test_lorenz_strict_is_bit_identical_to_oracle(n):
+    """Uncontracted FP64 in the oracle's operation order: identical bits."""
+    wl = W.lorenz(n)
+    g = _rk4(ens.ENS_SYS_LORENZ, wl, prec=ens.ENS_FP64_STRICT)
+    yo, st = oracle.rk4_solve(oracle.LORENZ, wl["params"], wl["y0"], 0.0, wl["dt"], wl["nsteps"])
+    assert g["sync"] == ens.ENS_OK
+    assert np.array_equal(g["y"], yo)
+    assert np.all(g["status"] == 0) and np.all(g["nacc"] == 1000) and np.all(g["nrhs"] == 4000)
+
+
+@pytest.mark.parametrize("n", [421, 16384])
+def test_lorenz_fast_matches_oracle_within_conditioned_bound(n):
+    """FMA kernel (the benchmarked configuration) vs the oracle: 1e-12
+    relative wherever the run does not amplify rounding, the derived bound
+    1024 eps A elsewhere (transient chaos near rho = 21)."""
+    wl = W.lorenz(n)
+    g = _rk4(ens.ENS_SYS_LORENZ, wl)
+    yo, A = rk4_amplification(ens.ENS_SYS_LORENZ, wl["params"], wl["y0"], wl["dt"], wl["nsteps"])
+    err = rel_err(g["y"], yo)
+    tol = rk4_tolerance(A)
+    assert np.all(err <= tol), (err / tol).max()
+    well = A < 1e3
+    assert well.mean() > 0.8
+    assert np.all(err[well] <= 1e-12)
+    np.testing.assert_array_equal(g["t"], np.full(n, 10.0))
+
+
+def test_x2p_strict_and_fast():
+    wl = W.x2p(1 << 16)
+    gs = _rk4(ens.ENS_SYS_TOY_X2P, wl, prec=ens.ENS_FP64_STRICT)
+    gf = _rk4(ens.ENS_SYS_TOY_X2P, wl)
+    yo, _ = oracle.rk4_solve(oracle.X2P, wl["params"], wl["y0"], 0.0, wl["dt"], wl["nsteps"])
+    assert np.array_equal(gs["y"], yo)
+    assert rel_err(gf["y"], yo).max() < 1e-12
+
+
+def test_x2p_full_size_sampled():
+    """The 2^20-system calibration workload, checked on a stratified sample."""
+    wl = W.x2p(1 << 20)
+    g = _rk4(ens.ENS_SYS_TOY_X2P, wl)
+    idx = W.subsample(1 << 20, 4096)
+    sub = W.take(wl, idx)
+    yo, _ = oracle.rk4_solve(oracle.X2P, sub["params"], sub["y0"], 0.0, wl["dt"], wl["nsteps"])
+    assert rel_err(g["y"][:, idx], yo).max() < 1e-12
+
+
+@pytest.mark.parametrize("block", [32, 64, 128, 256])
+def test_launch_shapes_do_not_change_results(block):
+    wl = W.lorenz(1000)
+    ref = _rk4(ens.ENS_SYS_LORENZ, wl)
+    g = _rk4(ens.ENS_SYS_LORENZ, wl, launch=ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=block))
+    assert np.array_equal(ref["y"], g["y"])
+
+
+def test_edge_sizes_and_nonfinite_status():
+    for n in (1, 31, 33):
+        wl = W.lorenz(n)
+        g = _rk4(ens.ENS_SYS_LORENZ, wl, nsteps=50)
+        yo, _ = oracle.rk4_solve(oracle.LORENZ, wl["params"], wl["y0"], 0.0, wl["dt"], 50)
+        assert rel_err(g["y"], yo).max() < 1e-13
+    # empty ensemble
+    tol = ens.make_tol(dt0=0.01, n_steps=10)
+    ctx = ens.ens_create(ens.ENS_SYS_LORENZ, 0, np.zeros((3, 0)), np.zeros((3, 0)), (0, 0), ens.ENS_RK4, tol)
+    ens.ens_solve(ctx)
+    assert ens.ens_sync(ctx) == ens.ENS_OK
+    ens.ens_destroy(ctx)
+    # x' = x^2 - p blows up from x0 = 2 with p = 0.1: reported, not hidden
+    p = np.array([[0.1, 0.5]])
+    y0 = np.array([[2.0, -0.5]])
+    tol = ens.make_tol(dt0=0.01, n_steps=1000)
+    g = solve_gpu(ens.ENS_SYS_TOY_X2P, p, y0, (0.0, 0.0), ens.ENS_RK4, tol)
+    assert g["status"][0] & ens.ENS_SYS_NONFINITE and g["status"][1] == 0
+    assert g["sync"] == ens.ENS_ESYSTEM
+
+
+def test_device_inputs_and_destinations():
+    import torch
+    wl = W.lorenz(777)
+    tol = ens.make_tol(dt0=wl["dt"], n_steps=100)
+    P = torch.from_numpy(wl["params"]).cuda()
+    Y = torch.from_numpy(wl["y0"]).cuda()
+    ctx = ens.ens_create(ens.ENS_SYS_LORENZ, 777, P, Y, (0.0, 0.0), ens.ENS_RK4, tol)
+    try:
+        s = torch.cuda.Stream()
+        ens.ens_solve(ctx, s)
+        ens.ens_sync(ctx)
+        dst = torch.empty((3, 777), dtype=torch.float64, device="cuda")
+        ens.ens_read(ctx, ens.ENS_STATE, dst)
+    finally:
+        ens.ens_destroy(ctx)
+    yo, _ = oracle.rk4_solve(oracle.LORENZ, wl["params"], wl["y0"], 0.0, wl["dt"], 100)
+    assert rel_err(dst.cpu().numpy(), yo).max() < 1e-12
