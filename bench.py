@@ -412,8 +412,55 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(case: str):
+    """One small run of a workload (after one warm-up run) for ncu captures;
+    prints the step counts that turn instruction counters into per-step
+    figures."""
+    import torch
+    import paper_2011_01740_gb300 as ens
+    torch.cuda.set_device(0)
+    if case == "km":
+        km = km_slice(1, 0, n_phases=2)
+        idx = W.subsample(km["phys"]["pA1"].size, 4096)
+        km = W.take(km, idx)
+        ph = km["phys"]
+        C = ens.ens_km_coefficients(ph["pA1"], ph["f1"], ph["pA2"], ph["f2"], ph["theta"], ph["RE"],
+                                    km["liquid"])
+        t = km["tol"]
+        tol = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
+                           n_phases=t.n_phases, phase_len=t.phase_len)
+        ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
+                             ens.ENS_RKCK45, tol)
+        ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=2))
+    elif case == "prv":
+        wl = W.prv(8192, t1=64.0)
+        t = wl["tol"]
+        tol = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
+                           event_tol=t.event_tol, acc_t_start=t.acc_t_start)
+        ctx = ens.ens_create(ens.ENS_SYS_RELIEF_VALVE, 8192, wl["params"], wl["y0"], (t.t0, t.t1),
+                             ens.ENS_RKCK45, tol)
+    elif case in ("x2p", "lorenz"):
+        wl = W.x2p(1 << 20) if case == "x2p" else W.lorenz(16384)
+        sysid = ens.ENS_SYS_TOY_X2P if case == "x2p" else ens.ENS_SYS_LORENZ
+        ctx = ens.ens_create(sysid, wl["params"].shape[1], wl["params"], wl["y0"], (0, 0), ens.ENS_RK4,
+                             ens.make_tol(dt0=wl["dt"], n_steps=wl["nsteps"]))
+        ens.ens_set_launch(ctx, ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=128))
+    else:
+        raise SystemExit(f"unknown profile case {case}")
+    for _ in range(2):
+        ens.ens_solve(ctx)
+        st = ens.ens_sync(ctx)
+    nacc = ens.ens_read(ctx, ens.ENS_NSTEPS)
+    nrej = ens.ens_read(ctx, ens.ENS_NREJ)
+    print(json.dumps({"case": case, "systems": int(nacc.size), "status": int(st),
+                      "accepted": int(nacc.sum()), "rejected": int(nrej.sum()),
+                      "trials": int(nacc.sum() + nrej.sum())}), flush=True)
+    ens.ens_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile", default=None, help="run one small case for ncu (km, prv, x2p, lorenz)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -429,6 +476,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
+    if args.profile:
+        run_profile_case(args.profile)
+        return
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

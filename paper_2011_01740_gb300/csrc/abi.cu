@@ -15,8 +15,8 @@
 
 namespace ens {
 cudaError_t launch_rk4(int sys, bool strict, const Rk4Args& a, int block, cudaStream_t s);
-cudaError_t launch_ck45(int sys, bool dual, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
-cudaError_t launch_ck45_fp32c(const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
+cudaError_t launch_ck45(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
+cudaError_t launch_ck45_fp32c(unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_order(const int64_t* steps, int64_t n, int32_t* order, unsigned* hist,
                          cudaStream_t s);
 }  // namespace ens
@@ -33,7 +33,7 @@ struct ens_ctx {
   int dim = 0, npar = 0;
   int64_t acc_rows = 0;
   double t0 = 0.0, t1 = 0.0;
-  bool dual = false;  // Keller-Miksis: second driving frequency present
+  unsigned km_flags = 0;  // Keller-Miksis kernel selection (kKmDual, kKmGeneralExponent)
   // device buffers
   double* params = nullptr;
   double* y0 = nullptr;
@@ -128,28 +128,31 @@ void free_buffers(ens_ctx* c) {
   c->gexec = nullptr;
 }
 
-__global__ void any_nonzero_kernel(const double* a, const double* b, int64_t n, unsigned* flag) {
+// Keller-Miksis kernel selection: bit kKmDual if any system drives with a
+// second frequency (C6 or C8 != 0), bit kKmGeneralExponent if any C10 is not
+// within 4 ulp of 21/5 (then pow() is used instead of the fifth-root form).
+__global__ void km_flags_kernel(const double* C, int64_t n, unsigned* flags) {
+  const double lo = 4.2 - 4 * 8.881784197001252e-16, hi = 4.2 + 4 * 8.881784197001252e-16;
+  unsigned f = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (a[i] != 0.0 || b[i] != 0.0) {
-      atomicOr(flag, 1u);
-      return;
-    }
+    if (C[6 * n + i] != 0.0 || C[8 * n + i] != 0.0) f |= kKmDual;
+    const double e = C[10 * n + i];
+    if (!(e >= lo && e <= hi)) f |= kKmGeneralExponent;
   }
+  if (f) atomicOr(flags, f);
 }
 
-// Keller-Miksis: is the second driving frequency (C6 or C8) used anywhere?
-ens_status detect_dual(ens_ctx* c) {
-  c->dual = false;
+ens_status detect_flags(ens_ctx* c) {
+  c->km_flags = 0;
   if (c->sys != ENS_SYS_KELLER_MIKSIS || c->n == 0) return ENS_OK;
   ENS_CUDA(c, cudaMemset(&c->scratch->any_status, 0, sizeof(unsigned)));
   const int64_t blocks = std::min<int64_t>((c->n + 255) / 256, 4096);
-  any_nonzero_kernel<<<(unsigned)blocks, 256>>>(c->params + 6 * c->n, c->params + 8 * c->n, c->n,
-                                                 &c->scratch->any_status);
+  km_flags_kernel<<<(unsigned)blocks, 256>>>(c->params, c->n, &c->scratch->any_status);
   ENS_CUDA(c, cudaGetLastError());
   unsigned flag = 0;
   ENS_CUDA(c, cudaMemcpy(&flag, &c->scratch->any_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
-  c->dual = flag != 0;
+  c->km_flags = flag;
   return ENS_OK;
 }
 
@@ -288,8 +291,8 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int sh
     if (p.n_phases > 0) p.n_phases = 1;
     else p.t1 = p.t0 + (p.t1 - p.t0) / 16.0;
     AdaptLaunch PL{(c->n + 127) / 128, 128};
-    cudaError_t e = c->tol.prec == ENS_FP32_COMP ? launch_ck45_fp32c(p, PL, s)
-                                                 : launch_ck45(c->sys, c->dual, p, PL, s);
+    cudaError_t e = c->tol.prec == ENS_FP32_COMP ? launch_ck45_fp32c(c->km_flags, p, PL, s)
+                                                 : launch_ck45(c->sys, c->km_flags, p, PL, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "pilot launch");
     e = launch_order(c->nacc, c->n, c->order, c->hist, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "order launch");
@@ -297,8 +300,8 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int sh
     a.order = c->order;
   }
   AdaptLaunch AL = adapt_launch(c, L);
-  cudaError_t e = c->tol.prec == ENS_FP32_COMP ? launch_ck45_fp32c(a, AL, s)
-                                               : launch_ck45(c->sys, c->dual, a, AL, s);
+  cudaError_t e = c->tol.prec == ENS_FP32_COMP ? launch_ck45_fp32c(c->km_flags, a, AL, s)
+                                               : launch_ck45(c->sys, c->km_flags, a, AL, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "adaptive launch");
   return ENS_OK;
 }
@@ -396,7 +399,7 @@ ens_status ens_create(ens_ctx** out, ens_system sys, int64_t n, const double* pa
     return ENS_ECUDA;
   }
   c->launch = default_launch(c);
-  st = detect_dual(c);
+  st = detect_flags(c);
   if (st != ENS_OK) {
     set_err(nullptr, "%s", c->err);
     free_buffers(c);
@@ -418,10 +421,10 @@ ens_status ens_set_inputs(ens_ctx* c, const double* params, const double* y0, vo
   c->last_stream = s;
   if (params && c->sys == ENS_SYS_KELLER_MIKSIS) {
     ENS_CUDA(c, cudaStreamSynchronize(s));
-    const bool was = c->dual;
-    ens_status st = detect_dual(c);
+    const unsigned was = c->km_flags;
+    ens_status st = detect_flags(c);
     if (st != ENS_OK) return st;
-    if (was != c->dual) c->graph_valid = false;
+    if (was != c->km_flags) c->graph_valid = false;
   }
   return ENS_OK;
 }

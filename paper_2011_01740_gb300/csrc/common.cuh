@@ -18,6 +18,10 @@ constexpr int kRing = 32;             // relief valve: Poincare maxima kept
 constexpr int kPrvAccRows = kRing + 3;
 constexpr int kEventRetries = 40;     // consecutive event-location retries allowed
 
+// Keller-Miksis kernel selection flags (set by the host from the parameters).
+constexpr unsigned kKmDual = 1u;             // some system has C6 or C8 != 0
+constexpr unsigned kKmGeneralExponent = 2u;  // some system's C10 is not 21/5
+
 // Per-system status bits (mirror ENS_SYS_* of ens.h).
 constexpr int32_t kStDtUnderflow = ENS_SYS_DT_UNDERFLOW;
 constexpr int32_t kStMaxSteps = ENS_SYS_MAX_STEPS;

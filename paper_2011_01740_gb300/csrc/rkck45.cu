@@ -81,10 +81,13 @@ __device__ __forceinline__ double err_norm(const double* y, const double* y5, co
   return E;
 }
 
+// fac = clamp(0.9 E^(-1/5), 0.2, 5).  0.9 E^(-1/5) leaves [0.2, 5] for
+// E > 4.5^5 = 1845.3 and E < 0.18^5 = 1.9e-4, so E is clamped to [1e-4, 2000]
+// first (same result, and keeps inv_fifth_root inside the float range).
 __device__ __forceinline__ double step_factor(double E) {
   if (isnan(E)) return 0.2;
-  if (E == 0.0) return 5.0;
-  double fac = 0.9 * pow(E, -0.2);
+  const double Ec = E < 1e-4 ? 1e-4 : (E > 2000.0 ? 2000.0 : E);
+  double fac = 0.9 * inv_fifth_root(Ec);
   fac = fac < 0.2 ? 0.2 : fac;
   fac = fac > 5.0 ? 5.0 : fac;
   return fac;
@@ -495,15 +498,22 @@ struct AdaptFixed : Fixed {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_ck45(int sys, bool dual, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s) {
+cudaError_t launch_ck45(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
   if (L.grid <= 0 || L.grid > 0x7fffffffLL || L.block <= 0) return cudaErrorInvalidConfiguration;
   const dim3 g((unsigned)L.grid), b((unsigned)L.block);
+  const bool dual = flags & kKmDual;
+  const bool exp215 = !(flags & kKmGeneralExponent);
   if (a.n_phases > 0) {
     switch (sys) {
       case ENS_SYS_KELLER_MIKSIS:
-        if (dual) ck_phased_kernel<KellerMiksis<true>><<<g, b, 0, s>>>(a);
-        else ck_phased_kernel<KellerMiksis<false>><<<g, b, 0, s>>>(a);
+        if (dual) {
+          if (exp215) ck_phased_kernel<KellerMiksis<true, true>><<<g, b, 0, s>>>(a);
+          else ck_phased_kernel<KellerMiksis<true, false>><<<g, b, 0, s>>>(a);
+        } else {
+          if (exp215) ck_phased_kernel<KellerMiksis<false, true>><<<g, b, 0, s>>>(a);
+          else ck_phased_kernel<KellerMiksis<false, false>><<<g, b, 0, s>>>(a);
+        }
         break;
       case ENS_SYS_LORENZ: ck_phased_kernel<AdaptFixed<Lorenz>><<<g, b, 0, s>>>(a); break;
       case ENS_SYS_TOY_X2P: ck_phased_kernel<AdaptFixed<X2P>><<<g, b, 0, s>>>(a); break;
@@ -514,8 +524,13 @@ cudaError_t launch_ck45(int sys, bool dual, const AdaptArgs& a, AdaptLaunch L, c
   } else {
     switch (sys) {
       case ENS_SYS_KELLER_MIKSIS:
-        if (dual) ck_plain_kernel<KellerMiksis<true>><<<g, b, 0, s>>>(a);
-        else ck_plain_kernel<KellerMiksis<false>><<<g, b, 0, s>>>(a);
+        if (dual) {
+          if (exp215) ck_plain_kernel<KellerMiksis<true, true>><<<g, b, 0, s>>>(a);
+          else ck_plain_kernel<KellerMiksis<true, false>><<<g, b, 0, s>>>(a);
+        } else {
+          if (exp215) ck_plain_kernel<KellerMiksis<false, true>><<<g, b, 0, s>>>(a);
+          else ck_plain_kernel<KellerMiksis<false, false>><<<g, b, 0, s>>>(a);
+        }
         break;
       case ENS_SYS_LORENZ: ck_plain_kernel<AdaptFixed<Lorenz>><<<g, b, 0, s>>>(a); break;
       case ENS_SYS_TOY_X2P: ck_plain_kernel<AdaptFixed<X2P>><<<g, b, 0, s>>>(a); break;

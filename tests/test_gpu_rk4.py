@@ -37,18 +37,20 @@ def test_lorenz_strict_is_bit_identical_to_oracle(n):
 
 @pytest.mark.parametrize("n", [421, 16384])
 def test_lorenz_fast_matches_oracle_within_conditioned_bound(n):
-    """FMA kernel (the benchmarked configuration) vs the oracle: 1e-12
-    relative wherever the run does not amplify rounding, the derived bound
-    1024 eps A elsewhere (transient chaos near rho = 21)."""
+    """FMA kernel (the benchmarked configuration) vs the oracle: within the
+    derived bound max(1e-12, 8 N eps A) for every system (A: the oracle-measured
+    growth of a relative perturbation; up to 1e5 in the transient chaos near
+    rho = 21); most systems within 1e-12 outright."""
     wl = W.lorenz(n)
     g = _rk4(ens.ENS_SYS_LORENZ, wl)
     yo, A = rk4_amplification(ens.ENS_SYS_LORENZ, wl["params"], wl["y0"], wl["dt"], wl["nsteps"])
     err = rel_err(g["y"], yo)
-    tol = rk4_tolerance(A)
+    tol = rk4_tolerance(A, wl["nsteps"])
     assert np.all(err <= tol), (err / tol).max()
-    well = A < 1e3
-    assert well.mean() > 0.8
-    assert np.all(err[well] <= 1e-12)
+    within = (err <= 1e-12).mean()
+    print(f"rk4 fma vs oracle: {within:.4f} of systems within 1e-12, max err {err.max():.2e}, "
+          f"max err / bound {(err / tol).max():.3f}")
+    assert within > 0.8
     np.testing.assert_array_equal(g["t"], np.full(n, 10.0))
 
 
