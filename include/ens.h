@@ -249,6 +249,84 @@ ens_status ens_km_coefficients(int64_t n, const double *pA1, const double *f1, c
                                const double *f2, const double *theta, const double *RE,
                                const ens_liquid *liquid, double *out, void *stream);
 
+
+/* ------------------------------------------------------------------------ */
+/* Surrogate screening (learned extension of the Keller-Miksis sweep)         */
+/*
+ * A small ensemble of multilayer perceptrons maps the driving of a bubble,
+ * x = (log p_A, log f) scaled to [-1, 1] (ens_km_features), to
+ * y0 = ln(max y1 over the recorded periods) and the logit of y1 = "period-1
+ * response" (ens_km_labels).  Each member is 2 -> 128 -> 128 -> 128 -> 128 -> 2
+ * with GELU (erf form) after the first four layers; weights are kept as FP32
+ * masters with BF16 copies, the 128 x 128 products run on the tensor cores
+ * with FP32 accumulation.  The screening forward returns the mean and the
+ * population standard deviation of y0 over the members and the mean
+ * period-1 probability; points whose spread exceeds a threshold are handed
+ * back to the FP64 solver (ens_select_above, ens_gather_f64, the solver
+ * calls above, ens_scatter_labels).  The paper has no surrogate: this part
+ * is an extension of its parameter sweeps (Sec. 4.2).
+ *
+ * Parameter vector of one member (floats, in this order, W stored [out][in]):
+ *   W1[128][2] b1[128] W2[128][128] b2[128] W3[128][128] b3[128]
+ *   W4[128][128] b4[128] W5[2][128] b5[2]              (ens_mlp_param_count())
+ * Loss per sample: (out0 - y0)^2 + binary cross-entropy with logits of
+ * (out1, y1), averaged over the batch; Adam on every parameter.
+ * Unless stated otherwise, array arguments are device memory
+ * (ENS_EINVAL otherwise) and work is enqueued on `stream`.
+ */
+typedef struct ens_mlp ens_mlp;
+
+typedef struct {
+    int32_t epochs;        /* passes over the training set                      */
+    int32_t batch;         /* samples per Adam step                             */
+    float lr, beta1, beta2, eps;   /* Adam (Kingma & Ba 2015)                    */
+    uint64_t seed;         /* shuffle stream (splitmix64)                        */
+} ens_train_cfg;
+
+/* Create `members` (1..8) networks; weights uniform in +-1/sqrt(fan_in),
+ * biases 0, member k drawn from the splitmix64 stream seed + k. */
+ens_status ens_mlp_create(ens_mlp **out, int32_t members, uint64_t seed);
+/* Number of floats in one member's parameter vector (50,178). */
+int64_t ens_mlp_param_count(void);
+/* Copy all members' parameters in / out ([members][param_count] floats,
+ * host or device); set_params also resets the Adam moments. */
+ens_status ens_mlp_set_params(ens_mlp *m, const float *params, size_t bytes);
+ens_status ens_mlp_get_params(ens_mlp *m, float *params, size_t bytes);
+/* Raw outputs of every member: x [n][2] -> out [members][n][2]. */
+ens_status ens_mlp_forward(ens_mlp *m, int64_t n, const float *x, float *out, void *stream);
+/* Loss (per member, host array [members]) and gradient ([members][param_count],
+ * host or device) of one batch; synchronous. */
+ens_status ens_mlp_loss_grad(ens_mlp *m, int64_t n, const float *x, const float *y, float *loss,
+                             float *grad, void *stream);
+/* Train on n samples (x [n][2], y [n][2]) with shuffled mini-batches; loss_hist
+ * (host, may be NULL) receives the mean per-sample loss of each epoch and
+ * member ([epochs][members]).  Synchronous. */
+ens_status ens_mlp_train(ens_mlp *m, int64_t n, const float *x, const float *y, const ens_train_cfg *cfg,
+                         float *loss_hist, void *stream);
+/* Fused ensemble inference: mean[n], stdv[n] (population standard deviation
+ * of output 0 over the members), p1[n] (mean sigmoid of output 1). */
+ens_status ens_mlp_screen(ens_mlp *m, int64_t n, const float *x, float *mean, float *stdv, float *p1,
+                          void *stream);
+const char *ens_mlp_last_error(const ens_mlp *m);
+void ens_mlp_destroy(ens_mlp *m);
+
+/* Features x[n][2] = 2 (ln v - ln lo) / (ln hi - ln lo) - 1 for v = pA and f
+ * with range = {pA_lo, pA_hi, f_lo, f_hi} (host array, all > 0). */
+ens_status ens_km_features(int64_t n, const double *pA, const double *f, const double range[4], float *x,
+                           void *stream);
+/* Targets y[n][2] from phase-mode accessories acc[2 n_phases][n]: y0 = ln of
+ * the largest per-phase maximum over phases [first_phase, n_phases), y1 = 1
+ * if those per-phase maxima spread by less than spread_tol (relative). */
+ens_status ens_km_labels(int64_t n, const double *acc, int32_t n_phases, int32_t first_phase,
+                         double spread_tol, float *y, void *stream);
+/* idx[0..*count) = increasing indices i with v[i] > thr (idx holds n
+ * entries); *count is written on the host; synchronous. */
+ens_status ens_select_above(int64_t n, const float *v, float thr, int32_t *idx, int64_t *count, void *stream);
+/* dst[i] = src[idx[i]] for i < k. */
+ens_status ens_gather_f64(int64_t k, const int32_t *idx, const double *src, double *dst, void *stream);
+/* dst[idx[i]] = y[i][0] for i < k (writes re-solved values into a screened map). */
+ens_status ens_scatter_labels(int64_t k, const int32_t *idx, const float *y, float *dst, void *stream);
+
 /* Library version string. */
 const char *ens_version(void);
 

@@ -302,3 +302,160 @@ def ens_km_coefficients(pA1, f1, pA2, f2, theta, RE, liquid: dict, out=None, str
                                    _ptr(out, keep), _stream(stream))
     _check(st, None)
     return out
+
+
+# ---------------------------------------------------------------------------
+# surrogate network (device arrays: torch CUDA tensors)
+# ---------------------------------------------------------------------------
+
+class EnsTrainCfg(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
+def make_train_cfg(epochs=50, batch=1024, lr=2e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=20201103):
+    return EnsTrainCfg(int(epochs), int(batch), lr, beta1, beta2, eps, int(seed))
+
+
+_mlp_bound = False
+
+
+def _mlp_lib():
+    global _mlp_bound
+    L = lib()
+    if not _mlp_bound:
+        vp = ctypes.c_void_p
+        st = ctypes.c_int
+        L.ens_mlp_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_uint64]
+        L.ens_mlp_create.restype = st
+        L.ens_mlp_param_count.restype = ctypes.c_int64
+        L.ens_mlp_set_params.argtypes = [vp, vp, ctypes.c_size_t]
+        L.ens_mlp_set_params.restype = st
+        L.ens_mlp_get_params.argtypes = [vp, vp, ctypes.c_size_t]
+        L.ens_mlp_get_params.restype = st
+        L.ens_mlp_forward.argtypes = [vp, ctypes.c_int64, vp, vp, vp]
+        L.ens_mlp_forward.restype = st
+        L.ens_mlp_loss_grad.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, vp]
+        L.ens_mlp_loss_grad.restype = st
+        L.ens_mlp_train.argtypes = [vp, ctypes.c_int64, vp, vp, ctypes.POINTER(EnsTrainCfg), vp, vp]
+        L.ens_mlp_train.restype = st
+        L.ens_mlp_screen.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, vp]
+        L.ens_mlp_screen.restype = st
+        L.ens_mlp_last_error.argtypes = [vp]
+        L.ens_mlp_last_error.restype = ctypes.c_char_p
+        L.ens_mlp_destroy.argtypes = [vp]
+        L.ens_mlp_destroy.restype = None
+        L.ens_km_features.argtypes = [ctypes.c_int64, vp, vp, ctypes.c_double * 4, vp, vp]
+        L.ens_km_features.restype = st
+        L.ens_km_labels.argtypes = [ctypes.c_int64, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, vp, vp]
+        L.ens_km_labels.restype = st
+        L.ens_select_above.argtypes = [ctypes.c_int64, vp, ctypes.c_float, vp, ctypes.POINTER(ctypes.c_int64), vp]
+        L.ens_select_above.restype = st
+        L.ens_gather_f64.argtypes = [ctypes.c_int64, vp, vp, vp, vp]
+        L.ens_gather_f64.restype = st
+        L.ens_scatter_labels.argtypes = [ctypes.c_int64, vp, vp, vp, vp]
+        L.ens_scatter_labels.restype = st
+        _mlp_bound = True
+    return L
+
+
+def _mcheck(status: int, m=None):
+    if status != ENS_OK:
+        raise EnsError(status, _mlp_lib().ens_mlp_last_error(m).decode(errors="replace"))
+
+
+def _nbytes(a):
+    return a.element_size() * a.numel() if hasattr(a, "element_size") else a.nbytes
+
+
+def ens_mlp_create(members: int = 4, seed: int = 20201103) -> int:
+    m = ctypes.c_void_p()
+    _mcheck(_mlp_lib().ens_mlp_create(ctypes.byref(m), int(members), int(seed)))
+    return m.value
+
+
+def ens_mlp_param_count() -> int:
+    return int(_mlp_lib().ens_mlp_param_count())
+
+
+def ens_mlp_set_params(m: int, params):
+    keep = []
+    _mcheck(_mlp_lib().ens_mlp_set_params(m, _ptr(params, keep), _nbytes(params)), m)
+
+
+def ens_mlp_get_params(m: int, params):
+    keep = []
+    _mcheck(_mlp_lib().ens_mlp_get_params(m, _ptr(params, keep), _nbytes(params)), m)
+    return params
+
+
+def ens_mlp_forward(m: int, n: int, x, out, stream=None):
+    keep = []
+    _mcheck(_mlp_lib().ens_mlp_forward(m, int(n), _ptr(x, keep), _ptr(out, keep), _stream(stream)), m)
+    return out
+
+
+def ens_mlp_loss_grad(m: int, n: int, x, y, members: int, grad, stream=None):
+    keep = []
+    loss = (ctypes.c_float * members)()
+    _mcheck(_mlp_lib().ens_mlp_loss_grad(m, int(n), _ptr(x, keep), _ptr(y, keep), ctypes.cast(loss, ctypes.c_void_p),
+                                         _ptr(grad, keep), _stream(stream)), m)
+    return np.array(list(loss), dtype=np.float32)
+
+
+def ens_mlp_train(m: int, n: int, x, y, cfg: EnsTrainCfg, members: int, stream=None):
+    keep = []
+    hist = np.zeros((max(cfg.epochs, 1), members), dtype=np.float32)
+    _mcheck(_mlp_lib().ens_mlp_train(m, int(n), _ptr(x, keep), _ptr(y, keep), ctypes.byref(cfg),
+                                     hist.ctypes.data, _stream(stream)), m)
+    return hist[: cfg.epochs]
+
+
+def ens_mlp_screen(m: int, n: int, x, mean, stdv, p1, stream=None):
+    keep = []
+    _mcheck(_mlp_lib().ens_mlp_screen(m, int(n), _ptr(x, keep), _ptr(mean, keep), _ptr(stdv, keep), _ptr(p1, keep),
+                                      _stream(stream)), m)
+
+
+def ens_mlp_last_error(m: int | None = None) -> str:
+    return _mlp_lib().ens_mlp_last_error(m).decode(errors="replace")
+
+
+def ens_mlp_destroy(m: int):
+    if m:
+        _mlp_lib().ens_mlp_destroy(m)
+
+
+def ens_km_features(n: int, pA, f, rng, x, stream=None):
+    keep = []
+    r = (ctypes.c_double * 4)(*[float(v) for v in rng])
+    _mcheck(_mlp_lib().ens_km_features(int(n), _ptr(pA, keep), _ptr(f, keep), r, _ptr(x, keep), _stream(stream)))
+    return x
+
+
+def ens_km_labels(n: int, acc, n_phases: int, first_phase: int, spread_tol: float, y, stream=None):
+    keep = []
+    _mcheck(_mlp_lib().ens_km_labels(int(n), _ptr(acc, keep), int(n_phases), int(first_phase), float(spread_tol),
+                                     _ptr(y, keep), _stream(stream)))
+    return y
+
+
+def ens_select_above(n: int, v, thr: float, idx, stream=None) -> int:
+    keep = []
+    cnt = ctypes.c_int64(0)
+    _mcheck(_mlp_lib().ens_select_above(int(n), _ptr(v, keep), float(thr), _ptr(idx, keep), ctypes.byref(cnt),
+                                        _stream(stream)))
+    return int(cnt.value)
+
+
+def ens_gather_f64(k: int, idx, src, dst, stream=None):
+    keep = []
+    _mcheck(_mlp_lib().ens_gather_f64(int(k), _ptr(idx, keep), _ptr(src, keep), _ptr(dst, keep), _stream(stream)))
+    return dst
+
+
+def ens_scatter_labels(k: int, idx, y, dst, stream=None):
+    keep = []
+    _mcheck(_mlp_lib().ens_scatter_labels(int(k), _ptr(idx, keep), _ptr(y, keep), _ptr(dst, keep), _stream(stream)))
+    return dst

@@ -1,0 +1,534 @@
+// abi_mlp.cu -- C ABI of the surrogate network (include/ens.h, "Surrogate"):
+// model state, training driver, screening, and the device helpers of the
+// screening pipeline (features, labels, compaction, merge).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mlp.cuh"
+
+using namespace ens;
+
+struct ens_mlp {
+  int members = 0;
+  float* master = nullptr;        // [members][kP]
+  __nv_bfloat16* wbf = nullptr;   // [members][kPS]
+  float* m1 = nullptr;
+  float* m2 = nullptr;
+  float* grad = nullptr;
+  int64_t adam_t = 0;
+  // batch scratch
+  int64_t cap = 0;
+  float* xb = nullptr;
+  float* yb = nullptr;
+  float* z = nullptr;
+  float* dz = nullptr;
+  float* out = nullptr;
+  float* dout = nullptr;
+  float* loss = nullptr;          // [members]
+  char err[512] = {0};
+};
+
+namespace {
+
+thread_local char g_mlp_err[512] = {0};
+
+void merr(ens_mlp* m, const char* fmt, ...) {
+  char* buf = m ? m->err : g_mlp_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+}
+
+#define MLP_CUDA(m, call)                                                   \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) {                                                \
+      merr((m), "%s: %s", #call, cudaGetErrorString(e_));                   \
+      return ENS_ECUDA;                                                     \
+    }                                                                       \
+  } while (0)
+
+bool is_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  const bool ok = cudaPointerGetAttributes(&at, p) == cudaSuccess;
+  cudaGetLastError();
+  return ok && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+}
+
+unsigned grid_for(int64_t n, int block = 256, int64_t cap = 8192) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  return (unsigned)std::min<int64_t>(g, cap);
+}
+
+ens_status ensure_batch(ens_mlp* m, int64_t B) {
+  if (B <= m->cap) return ENS_OK;
+  cudaFree(m->xb);
+  cudaFree(m->yb);
+  cudaFree(m->z);
+  cudaFree(m->dz);
+  cudaFree(m->out);
+  cudaFree(m->dout);
+  m->xb = m->yb = m->z = m->dz = m->out = m->dout = nullptr;
+  m->cap = 0;
+  const size_t M = (size_t)m->members;
+  cudaError_t e = cudaMalloc(&m->xb, B * 2 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->yb, B * 2 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->z, M * B * 4 * mlp::H * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->dz, M * 4 * B * mlp::H * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->out, M * B * 2 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->dout, M * B * 2 * sizeof(float));
+  if (e != cudaSuccess) {
+    merr(m, "batch scratch: %s", cudaGetErrorString(e));
+    return ENS_ENOMEM;
+  }
+  m->cap = B;
+  return ENS_OK;
+}
+
+// forward (training form) + backward + weight gradients of one batch already
+// in m->xb / m->yb; loss[members] accumulates the per-sample loss sum.
+ens_status batch_grad(ens_mlp* m, int64_t B, float* loss, cudaStream_t s) {
+  mlp::FwdArgs f{};
+  f.n = B;
+  f.members = m->members;
+  f.x = m->xb;
+  f.master = m->master;
+  f.wbf = m->wbf;
+  f.z = m->z;
+  f.out = m->out;
+  MLP_CUDA(m, mlp::launch_forward_train(f, s));
+  mlp::BwdArgs b{};
+  b.n = B;
+  b.y = m->yb;
+  b.master = m->master;
+  b.wbf = m->wbf;
+  b.z = m->z;
+  b.out = m->out;
+  b.dout = m->dout;
+  b.dz = m->dz;
+  b.loss = loss;
+  MLP_CUDA(m, mlp::launch_backward(b, m->members, s));
+  mlp::GradArgs g{};
+  g.n = B;
+  g.x = m->xb;
+  g.z = m->z;
+  g.dz = m->dz;
+  g.dout = m->dout;
+  g.grad = m->grad;
+  MLP_CUDA(m, mlp::launch_wgrad(g, m->members, s));
+  return ENS_OK;
+}
+
+bool g_attr_set = false;
+
+ens_status set_smem_attrs(ens_mlp* m) {
+  if (g_attr_set) return ENS_OK;
+  MLP_CUDA(m, mlp::set_smem_limits());
+  g_attr_set = true;
+  return ENS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// screening-pipeline helpers
+// ---------------------------------------------------------------------------
+
+__global__ void km_features_kernel(int64_t n, const double* pA, const double* f, double la0, double la1,
+                                   double lf0, double lf1, float* x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[2 * i] = (float)(2.0 * (log(pA[i]) - la0) / (la1 - la0) - 1.0);
+    x[2 * i + 1] = (float)(2.0 * (log(f[i]) - lf0) / (lf1 - lf0) - 1.0);
+  }
+}
+
+// Targets from per-phase accessories acc[2 n_phases][n]: y0 = ln(max of the
+// per-phase maxima over phases [first, n_phases)), y1 = 1 if those maxima
+// spread by less than spread_tol relative (period-1 response), else 0.
+__global__ void km_labels_kernel(int64_t n, const double* acc, int n_phases, int first, double spread_tol,
+                                 float* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double mx = -INFINITY, mn = INFINITY;
+    for (int p = first; p < n_phases; ++p) {
+      const double v = acc[(int64_t)(2 * p) * n + i];
+      mx = fmax(mx, v);
+      mn = fmin(mn, v);
+    }
+    y[2 * i] = (float)log(mx);
+    y[2 * i + 1] = ((mx - mn) / mx < spread_tol) ? 1.0f : 0.0f;
+  }
+}
+
+// Deterministic stream compaction of {i : v[i] > thr} in increasing order.
+constexpr int kSelBlock = 1024;
+
+__global__ void select_count_kernel(int64_t n, const float* v, float thr, unsigned* counts) {
+  const int64_t i = blockIdx.x * (int64_t)kSelBlock + threadIdx.x;
+  const int c = __syncthreads_count(i < n && v[i] > thr);
+  if (threadIdx.x == 0) counts[blockIdx.x] = (unsigned)c;
+}
+
+__global__ void select_scan_kernel(unsigned* counts, int64_t nblocks, long long* total) {
+  // one block of 1024 threads; each thread scans a contiguous segment
+  __shared__ unsigned long long part[1024];
+  const int t = threadIdx.x;
+  const int64_t per = (nblocks + 1023) / 1024;
+  const int64_t lo = t * per, hi = std::min<int64_t>(nblocks, lo + per);
+  unsigned long long s = 0;
+  for (int64_t b = lo; b < hi; ++b) s += counts[b];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    unsigned long long run = 0;
+    for (int k = 0; k < 1024; ++k) {
+      const unsigned long long c = part[k];
+      part[k] = run;
+      run += c;
+    }
+    *total = (long long)run;
+  }
+  __syncthreads();
+  unsigned long long run = part[t];
+  for (int64_t b = lo; b < hi; ++b) {
+    const unsigned c = counts[b];
+    counts[b] = (unsigned)run;
+    run += c;
+  }
+}
+
+__global__ void select_scatter_kernel(int64_t n, const float* v, float thr, const unsigned* offs, int32_t* idx) {
+  __shared__ unsigned warp_base[kSelBlock / 32];
+  const int64_t i = blockIdx.x * (int64_t)kSelBlock + threadIdx.x;
+  const bool flag = i < n && v[i] > thr;
+  const unsigned ballot = __ballot_sync(0xffffffffu, flag);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) warp_base[warp] = __popc(ballot);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+    for (int w = 0; w < kSelBlock / 32; ++w) {
+      const unsigned c = warp_base[w];
+      warp_base[w] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (flag) {
+    const unsigned rank = __popc(ballot & ((1u << lane) - 1u));
+    idx[offs[blockIdx.x] + warp_base[warp] + rank] = (int32_t)i;
+  }
+}
+
+__global__ void gather_f64_kernel(int64_t k, const int32_t* idx, const double* src, double* dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[idx[i]];
+}
+
+__global__ void scatter_f32_kernel(int64_t k, const int32_t* idx, const float* src, float* dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+    dst[idx[i]] = src[2 * i];
+}
+
+}  // namespace
+
+extern "C" {
+
+ens_status ens_mlp_create(ens_mlp** out, int32_t members, uint64_t seed) {
+  if (!out || members < 1 || members > mlp::kMaxMembers) {
+    merr(nullptr, "ens_mlp_create: need out != NULL and 1 <= members <= %d", mlp::kMaxMembers);
+    return ENS_EINVAL;
+  }
+  *out = nullptr;
+  ens_mlp* m = new (std::nothrow) ens_mlp();
+  if (!m) return ENS_ENOMEM;
+  m->members = members;
+  const size_t tot = (size_t)members * mlp::kP;
+  cudaError_t e = cudaMalloc(&m->master, tot * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->wbf, (size_t)members * mlp::kPS * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMemset(m->wbf, 0, (size_t)members * mlp::kPS * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&m->m1, tot * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->m2, tot * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->grad, tot * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->loss, (size_t)members * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(m->m1, 0, tot * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(m->m2, 0, tot * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(m->grad, 0, tot * sizeof(float));
+  if (e == cudaSuccess) {
+    e = mlp::launch_init(members, seed, m->master, nullptr);
+    if (e == cudaSuccess) e = mlp::launch_to_bf16((int64_t)tot, m->master, m->wbf, nullptr);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  ens_status st = e == cudaSuccess ? set_smem_attrs(m) : ENS_ECUDA;
+  if (e != cudaSuccess || st != ENS_OK) {
+    merr(nullptr, "ens_mlp_create: %s", e != cudaSuccess ? cudaGetErrorString(e) : m->err);
+    cudaFree(m->master);
+    cudaFree(m->wbf);
+    cudaFree(m->m1);
+    cudaFree(m->m2);
+    cudaFree(m->grad);
+    cudaFree(m->loss);
+    delete m;
+    return e == cudaErrorMemoryAllocation ? ENS_ENOMEM : ENS_ECUDA;
+  }
+  *out = m;
+  return ENS_OK;
+}
+
+int64_t ens_mlp_param_count(void) { return mlp::kP; }
+
+ens_status ens_mlp_set_params(ens_mlp* m, const float* params, size_t bytes) {
+  if (!m || !params) return ENS_EINVAL;
+  const size_t tot = (size_t)m->members * mlp::kP;
+  if (bytes < tot * sizeof(float)) {
+    merr(m, "params hold %zu bytes, need %zu", bytes, tot * sizeof(float));
+    return ENS_EINVAL;
+  }
+  MLP_CUDA(m, cudaMemcpy(m->master, params, tot * sizeof(float), cudaMemcpyDefault));
+  MLP_CUDA(m, mlp::launch_to_bf16((int64_t)tot, m->master, m->wbf, nullptr));
+  MLP_CUDA(m, cudaMemset(m->m1, 0, tot * sizeof(float)));
+  MLP_CUDA(m, cudaMemset(m->m2, 0, tot * sizeof(float)));
+  MLP_CUDA(m, cudaDeviceSynchronize());
+  m->adam_t = 0;
+  return ENS_OK;
+}
+
+ens_status ens_mlp_get_params(ens_mlp* m, float* params, size_t bytes) {
+  if (!m || !params) return ENS_EINVAL;
+  const size_t tot = (size_t)m->members * mlp::kP;
+  if (bytes < tot * sizeof(float)) {
+    merr(m, "params hold %zu bytes, need %zu", bytes, tot * sizeof(float));
+    return ENS_EINVAL;
+  }
+  MLP_CUDA(m, cudaDeviceSynchronize());
+  MLP_CUDA(m, cudaMemcpy(params, m->master, tot * sizeof(float), cudaMemcpyDefault));
+  return ENS_OK;
+}
+
+ens_status ens_mlp_forward(ens_mlp* m, int64_t n, const float* x, float* out, void* stream) {
+  if (!m || n < 0) return ENS_EINVAL;
+  if (n == 0) return ENS_OK;
+  if (!is_device(x) || !is_device(out)) {
+    merr(m, "ens_mlp_forward: x and out must be device memory");
+    return ENS_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  ens_status st = ensure_batch(m, n);
+  if (st != ENS_OK) return st;
+  mlp::FwdArgs f{};
+  f.n = n;
+  f.members = m->members;
+  f.x = x;
+  f.master = m->master;
+  f.wbf = m->wbf;
+  f.z = m->z;
+  f.out = out;
+  MLP_CUDA(m, mlp::launch_forward_train(f, s));
+  return ENS_OK;
+}
+
+ens_status ens_mlp_loss_grad(ens_mlp* m, int64_t n, const float* x, const float* y, float* loss, float* grad,
+                             void* stream) {
+  if (!m || n <= 0 || !loss || !grad) return ENS_EINVAL;
+  if (!is_device(x) || !is_device(y)) {
+    merr(m, "ens_mlp_loss_grad: x and y must be device memory");
+    return ENS_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  ens_status st = ensure_batch(m, n);
+  if (st != ENS_OK) return st;
+  MLP_CUDA(m, cudaMemcpyAsync(m->xb, x, n * 2 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  MLP_CUDA(m, cudaMemcpyAsync(m->yb, y, n * 2 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  MLP_CUDA(m, cudaMemsetAsync(m->loss, 0, m->members * sizeof(float), s));
+  st = batch_grad(m, n, m->loss, s);
+  if (st != ENS_OK) return st;
+  std::vector<float> l(m->members);
+  MLP_CUDA(m, cudaMemcpyAsync(l.data(), m->loss, m->members * sizeof(float), cudaMemcpyDeviceToHost, s));
+  MLP_CUDA(m, cudaMemcpyAsync(grad, m->grad, (size_t)m->members * mlp::kP * sizeof(float), cudaMemcpyDefault, s));
+  MLP_CUDA(m, cudaStreamSynchronize(s));
+  for (int k = 0; k < m->members; ++k) loss[k] = l[k] / (float)n;
+  return ENS_OK;
+}
+
+ens_status ens_mlp_train(ens_mlp* m, int64_t n, const float* x, const float* y, const ens_train_cfg* cfg,
+                         float* loss_hist, void* stream) {
+  if (!m || n <= 0 || !cfg || cfg->epochs < 0 || cfg->batch <= 0 || !(cfg->lr > 0.f)) return ENS_EINVAL;
+  if (n > 0x7fffffffLL) return ENS_EINVAL;
+  if (!is_device(x) || !is_device(y)) {
+    merr(m, "ens_mlp_train: x and y must be device memory");
+    return ENS_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t B = std::min<int64_t>(cfg->batch, n);
+  ens_status st = ensure_batch(m, B);
+  if (st != ENS_OK) return st;
+  int32_t* perm_d = nullptr;
+  float* hist_d = nullptr;
+  MLP_CUDA(m, cudaMalloc(&perm_d, n * sizeof(int32_t)));
+  cudaError_t e = cudaMalloc(&hist_d, (size_t)std::max(1, cfg->epochs) * m->members * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaFree(perm_d);
+    merr(m, "train scratch: %s", cudaGetErrorString(e));
+    return ENS_ENOMEM;
+  }
+  e = cudaMemsetAsync(hist_d, 0, (size_t)std::max(1, cfg->epochs) * m->members * sizeof(float), s);
+  std::vector<int32_t> perm(n);
+  const int64_t tot = (int64_t)m->members * mlp::kP;
+  for (int ep = 0; ep < cfg->epochs && e == cudaSuccess; ++ep) {
+    // Fisher-Yates with splitmix64 draws (stream seed + epoch)
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+    uint64_t ctr = (cfg->seed + 0x51ed2701ULL * (uint64_t)(ep + 1)) << 20;
+    for (int64_t i = n - 1; i > 0; --i) {
+      const uint64_t r = mlp::splitmix64(ctr++);
+      const int64_t j = (int64_t)(r % (uint64_t)(i + 1));
+      std::swap(perm[i], perm[j]);
+    }
+    e = cudaMemcpyAsync(perm_d, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    for (int64_t b0 = 0; b0 < n && e == cudaSuccess; b0 += B) {
+      const int64_t nb = std::min<int64_t>(B, n - b0);
+      e = mlp::launch_gather(nb, perm_d + b0, x, y, m->xb, m->yb, s);
+      if (e != cudaSuccess) break;
+      st = batch_grad(m, nb, hist_d + (size_t)ep * m->members, s);
+      if (st != ENS_OK) break;
+      m->adam_t += 1;
+      const float c1 = 1.0f - powf(cfg->beta1, (float)m->adam_t);
+      const float c2 = 1.0f - powf(cfg->beta2, (float)m->adam_t);
+      e = mlp::launch_adam(tot, m->master, m->wbf, m->grad, m->m1, m->m2, cfg->lr, cfg->beta1, cfg->beta2,
+                           cfg->eps, c1, c2, s);
+    }
+    if (st != ENS_OK) break;
+    // the loss accumulates per-sample sums over batches whose gradient was
+    // averaged per batch; the epoch value reported is the mean per sample
+  }
+  if (e == cudaSuccess && st == ENS_OK && loss_hist && cfg->epochs > 0) {
+    std::vector<float> h((size_t)cfg->epochs * m->members);
+    e = cudaMemcpyAsync(h.data(), hist_d, h.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (size_t k = 0; k < h.size(); ++k) loss_hist[k] = h[k] / (float)n;
+  } else if (e == cudaSuccess) {
+    e = cudaStreamSynchronize(s);
+  }
+  cudaFree(perm_d);
+  cudaFree(hist_d);
+  if (st != ENS_OK) return st;
+  if (e != cudaSuccess) {
+    merr(m, "training: %s", cudaGetErrorString(e));
+    return ENS_ECUDA;
+  }
+  return ENS_OK;
+}
+
+ens_status ens_mlp_screen(ens_mlp* m, int64_t n, const float* x, float* mean, float* stdv, float* p1,
+                          void* stream) {
+  if (!m || n < 0) return ENS_EINVAL;
+  if (n == 0) return ENS_OK;
+  if (!is_device(x) || !is_device(mean) || !is_device(stdv) || !is_device(p1)) {
+    merr(m, "ens_mlp_screen: arrays must be device memory");
+    return ENS_EINVAL;
+  }
+  mlp::FwdArgs f{};
+  f.n = n;
+  f.members = m->members;
+  f.x = x;
+  f.master = m->master;
+  f.wbf = m->wbf;
+  f.mean = mean;
+  f.stdv = stdv;
+  f.p1 = p1;
+  MLP_CUDA(m, mlp::launch_forward_screen(f, (cudaStream_t)stream));
+  return ENS_OK;
+}
+
+const char* ens_mlp_last_error(const ens_mlp* m) { return m ? m->err : g_mlp_err; }
+
+void ens_mlp_destroy(ens_mlp* m) {
+  if (!m) return;
+  cudaFree(m->master);
+  cudaFree(m->wbf);
+  cudaFree(m->m1);
+  cudaFree(m->m2);
+  cudaFree(m->grad);
+  cudaFree(m->loss);
+  cudaFree(m->xb);
+  cudaFree(m->yb);
+  cudaFree(m->z);
+  cudaFree(m->dz);
+  cudaFree(m->out);
+  cudaFree(m->dout);
+  delete m;
+}
+
+ens_status ens_km_features(int64_t n, const double* pA, const double* f, const double range[4], float* x,
+                           void* stream) {
+  if (n < 0 || !range) return ENS_EINVAL;
+  if (n == 0) return ENS_OK;
+  if (!is_device(pA) || !is_device(f) || !is_device(x)) return ENS_EINVAL;
+  if (!(range[0] > 0 && range[1] > range[0] && range[2] > 0 && range[3] > range[2])) return ENS_EINVAL;
+  km_features_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, pA, f, log(range[0]), log(range[1]),
+                                                                    log(range[2]), log(range[3]), x);
+  return cudaGetLastError() == cudaSuccess ? ENS_OK : ENS_ECUDA;
+}
+
+ens_status ens_km_labels(int64_t n, const double* acc, int32_t n_phases, int32_t first_phase, double spread_tol,
+                         float* y, void* stream) {
+  if (n < 0 || first_phase < 0 || first_phase >= n_phases) return ENS_EINVAL;
+  if (n == 0) return ENS_OK;
+  if (!is_device(acc) || !is_device(y)) return ENS_EINVAL;
+  km_labels_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, acc, n_phases, first_phase, spread_tol, y);
+  return cudaGetLastError() == cudaSuccess ? ENS_OK : ENS_ECUDA;
+}
+
+ens_status ens_select_above(int64_t n, const float* v, float thr, int32_t* idx, int64_t* count, void* stream) {
+  if (n < 0 || !count) return ENS_EINVAL;
+  if (n == 0) {
+    *count = 0;
+    return ENS_OK;
+  }
+  if (n > 0x7fffffffLL || !is_device(v) || !is_device(idx)) return ENS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nb = (n + kSelBlock - 1) / kSelBlock;
+  unsigned* counts = nullptr;
+  long long* total = nullptr;
+  if (cudaMalloc(&counts, nb * sizeof(unsigned)) != cudaSuccess) return ENS_ENOMEM;
+  if (cudaMalloc(&total, sizeof(long long)) != cudaSuccess) {
+    cudaFree(counts);
+    return ENS_ENOMEM;
+  }
+  select_count_kernel<<<(unsigned)nb, kSelBlock, 0, s>>>(n, v, thr, counts);
+  select_scan_kernel<<<1, 1024, 0, s>>>(counts, nb, total);
+  select_scatter_kernel<<<(unsigned)nb, kSelBlock, 0, s>>>(n, v, thr, counts, idx);
+  long long t = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&t, total, sizeof(long long), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(counts);
+  cudaFree(total);
+  if (e != cudaSuccess) return ENS_ECUDA;
+  *count = t;
+  return ENS_OK;
+}
+
+ens_status ens_gather_f64(int64_t k, const int32_t* idx, const double* src, double* dst, void* stream) {
+  if (k < 0) return ENS_EINVAL;
+  if (k == 0) return ENS_OK;
+  if (!is_device(idx) || !is_device(src) || !is_device(dst)) return ENS_EINVAL;
+  gather_f64_kernel<<<grid_for(k), 256, 0, (cudaStream_t)stream>>>(k, idx, src, dst);
+  return cudaGetLastError() == cudaSuccess ? ENS_OK : ENS_ECUDA;
+}
+
+ens_status ens_scatter_labels(int64_t k, const int32_t* idx, const float* y, float* dst, void* stream) {
+  if (k < 0) return ENS_EINVAL;
+  if (k == 0) return ENS_OK;
+  if (!is_device(idx) || !is_device(y) || !is_device(dst)) return ENS_EINVAL;
+  scatter_f32_kernel<<<grid_for(k), 256, 0, (cudaStream_t)stream>>>(k, idx, y, dst);
+  return cudaGetLastError() == cudaSuccess ? ENS_OK : ENS_ECUDA;
+}
+
+}  // extern "C"

@@ -157,3 +157,38 @@ def take(d: dict, idx: np.ndarray) -> dict:
     if "phys" in d:
         out["phys"] = {k: np.ascontiguousarray(v[idx]) for k, v in d["phys"].items()}
     return out
+
+
+# ---------------------------------------------------------------------------
+# surrogate network inputs
+# ---------------------------------------------------------------------------
+
+MLP_PARAMS = 50178          # floats per ensemble member (layout: include/ens.h)
+MLP_FAN_IN = [(256, 2), (128, 0), (16384, 128), (128, 0), (16384, 128), (128, 0), (16384, 128), (128, 0),
+              (256, 128), (2, 0)]  # (block size, fan-in; 0 = bias) in parameter order
+
+
+def mlp_params(members: int = 4, seed: int = SEED, bias_scale: float = 0.1) -> np.ndarray:
+    """Seeded parameter vectors [members][50178]: weights N(0, 1/fan_in),
+    biases N(0, bias_scale^2).  Member k draws from seed + k."""
+    out = np.empty((members, MLP_PARAMS), dtype=np.float32)
+    for k in range(members):
+        rng = np.random.default_rng(seed + k)
+        parts = []
+        for size, fan in MLP_FAN_IN:
+            scale = (1.0 / np.sqrt(fan)) if fan else bias_scale
+            parts.append(rng.normal(0.0, scale, size))
+        out[k] = np.concatenate(parts).astype(np.float32)
+    return out
+
+
+def mlp_batch(n: int, seed: int = SEED + 100):
+    """Seeded inputs x in [-1, 1]^2 and targets (a smooth function, a 0/1 label)."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1.0, 1.0, size=(n, 2)).astype(np.float32)
+    y0 = np.sin(2.0 * x[:, 0]) * x[:, 1] + 0.3 * x[:, 0]
+    y1 = (x[:, 0] + 0.5 * x[:, 1] > 0.1).astype(np.float32)
+    return x, np.stack([y0, y1], axis=1).astype(np.float32)
+
+
+KM_FEATURE_RANGE = (2.0e5 / 361, 2.0e5, 2.0e4, 1.0e6)   # (pA_lo, pA_hi, f_lo, f_hi)

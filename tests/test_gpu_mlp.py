@@ -1,0 +1,163 @@
+"""GPU parity of the surrogate network: BF16 tensor-core forward, backward and
+weight gradients against the float64 oracle (oracle/mlp.py), training,
+screening and the device helpers of the screening pipeline."""
+import numpy as np
+import pytest
+
+import paper_2011_01740_gb300 as ens
+from oracle import mlp as omlp
+from paper_2011_01740_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BF16_TOL = 2e-2      # relative, per parameter block: BF16 operands (8-bit mantissa), FP32 accumulation
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    ens.lib()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _model(members, params):
+    m = ens.ens_mlp_create(members, W.SEED)
+    ens.ens_mlp_set_params(m, params)
+    return m
+
+
+def _blocks():
+    offs = np.cumsum([0] + [s for s, _ in W.MLP_FAN_IN])
+    names = [n for n, _ in omlp.SHAPES]
+    return list(zip(names, offs[:-1], offs[1:]))
+
+
+def test_parameter_layout_matches():
+    assert ens.ens_mlp_param_count() == omlp.N_PARAMS == W.MLP_PARAMS
+
+
+def test_params_round_trip():
+    import torch
+    p = W.mlp_params(3)
+    m = _model(3, p)
+    try:
+        back = np.empty_like(p)
+        ens.ens_mlp_get_params(m, back)
+        assert np.array_equal(back, p)
+    finally:
+        ens.ens_mlp_destroy(m)
+
+
+@pytest.mark.parametrize("n", [1, 77, 128, 1000])
+def test_forward_matches_oracle(n):
+    import torch
+    M = 4
+    p = W.mlp_params(M)
+    x, _ = W.mlp_batch(n)
+    m = _model(M, p)
+    try:
+        out = torch.empty((M, n, 2), dtype=torch.float32, device="cuda")
+        ens.ens_mlp_forward(m, n, _dev(x), out)
+        torch.cuda.synchronize()
+        g = out.cpu().numpy()
+    finally:
+        ens.ens_mlp_destroy(m)
+    for k in range(M):
+        ref, _ = omlp.forward(p[k].astype(np.float64), x.astype(np.float64))
+        err = np.abs(g[k] - ref).max() / np.abs(ref).max()
+        assert err < BF16_TOL, (k, err)
+
+
+def test_gradient_matches_oracle():
+    """Loss and gradient of one batch of 300 samples (3 tiles with a ragged
+    tail) for every member and every parameter block."""
+    import torch
+    M, n = 4, 300
+    p = W.mlp_params(M)
+    x, y = W.mlp_batch(n)
+    m = _model(M, p)
+    try:
+        grad = np.empty((M, W.MLP_PARAMS), dtype=np.float32)
+        loss = ens.ens_mlp_loss_grad(m, n, _dev(x), _dev(y), M, grad)
+    finally:
+        ens.ens_mlp_destroy(m)
+    for k in range(M):
+        L, g = omlp.grad(p[k].astype(np.float64), x.astype(np.float64), y.astype(np.float64))
+        assert abs(loss[k] - L) < BF16_TOL * abs(L), (k, loss[k], L)
+        for name, lo, hi in _blocks():
+            ref = g[lo:hi]
+            err = np.linalg.norm(grad[k, lo:hi] - ref) / max(np.linalg.norm(ref), 1e-30)
+            assert err < BF16_TOL, (k, name, err)
+
+
+def test_screen_agrees_with_member_outputs():
+    import torch
+    M, n = 4, 5000
+    p = W.mlp_params(M)
+    x, _ = W.mlp_batch(n, seed=7)
+    m = _model(M, p)
+    try:
+        xd = _dev(x)
+        out = torch.empty((M, n, 2), dtype=torch.float32, device="cuda")
+        ens.ens_mlp_forward(m, n, xd, out)
+        mean, sd, p1 = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+        ens.ens_mlp_screen(m, n, xd, mean, sd, p1)
+        torch.cuda.synchronize()
+    finally:
+        ens.ens_mlp_destroy(m)
+    o = out.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(mean.cpu().numpy(), o[:, :, 0].mean(0), rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(sd.cpu().numpy(), o[:, :, 0].std(0), rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(p1.cpu().numpy(), (1 / (1 + np.exp(-o[:, :, 1]))).mean(0), rtol=1e-5, atol=1e-6)
+
+
+def test_training_reduces_loss():
+    M, n = 4, 8192
+    x, y = W.mlp_batch(n, seed=11)
+    m = ens.ens_mlp_create(M, W.SEED)
+    try:
+        hist = ens.ens_mlp_train(m, n, _dev(x), _dev(y), ens.make_train_cfg(epochs=40, batch=512, lr=2e-3), M)
+    finally:
+        ens.ens_mlp_destroy(m)
+    assert hist.shape == (40, M)
+    assert np.all(np.isfinite(hist))
+    assert np.all(hist[-1] < 0.25 * hist[0]), hist[[0, -1]]
+
+
+def test_select_gather_scatter_labels_features():
+    import torch
+    rng = np.random.default_rng(4)
+    n = 100_003
+    v = rng.uniform(0, 1, n).astype(np.float32)
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    k = ens.ens_select_above(n, _dev(v), 0.9, idx)
+    ref = np.nonzero(v > 0.9)[0]
+    assert k == ref.size and np.array_equal(idx[:k].cpu().numpy(), ref)
+    src = rng.normal(size=n)
+    dst = torch.empty(k, dtype=torch.float64, device="cuda")
+    ens.ens_gather_f64(k, idx, _dev(src), dst)
+    assert np.array_equal(dst.cpu().numpy(), src[ref])
+    ys = torch.from_numpy(np.stack([np.arange(k), np.zeros(k)], 1).astype(np.float32)).cuda()
+    tgt = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+    ens.ens_scatter_labels(k, idx, ys, tgt)
+    t = tgt.cpu().numpy()
+    assert np.array_equal(t[ref], np.arange(k, dtype=np.float32)) and np.all(t[v <= 0.9] == -1.0)
+    # features and labels
+    pA, f = W.screen_grid(64)
+    x = torch.empty((pA.size, 2), dtype=torch.float32, device="cuda")
+    ens.ens_km_features(pA.size, _dev(pA), _dev(f), W.KM_FEATURE_RANGE, x)
+    lo_a, hi_a, lo_f, hi_f = W.KM_FEATURE_RANGE
+    ex = np.stack([2 * np.log(pA / lo_a) / np.log(hi_a / lo_a) - 1, 2 * np.log(f / lo_f) / np.log(hi_f / lo_f) - 1], 1)
+    np.testing.assert_allclose(x.cpu().numpy(), ex, atol=2e-7)
+    acc = np.abs(rng.normal(size=(8, 50))) + 1.0
+    acc[4::2, :25] = acc[4, :25]           # maxima equal over phases 2, 3: period 1
+    y = torch.empty((50, 2), dtype=torch.float32, device="cuda")
+    ens.ens_km_labels(50, _dev(acc), 4, 2, 1e-4, y)
+    yy = y.cpu().numpy()
+    np.testing.assert_allclose(yy[:, 0], np.log(acc[4::2].max(0)), rtol=1e-6)
+    assert np.array_equal(yy[:, 1], (np.ptp(acc[4::2], 0) / acc[4::2].max(0) < 1e-4).astype(np.float32))
