@@ -339,7 +339,7 @@ def run_secondary(ens, torch, stream, dev):
                        event_tol=t.event_tol, acc_t_start=t.acc_t_start, timeout_s=900.0)
     ctx = ens.ens_create(ens.ENS_SYS_RELIEF_VALVE, 262144, wl["params"], wl["y0"], (t.t0, t.t1),
                          ens.ENS_RKCK45, tol)
-    ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=2, use_graph=1))
+    ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1, use_graph=1, cost_order=1))
     ms = timed(ctx, 1)
     nacc = ens.ens_read(ctx, ens.ENS_NSTEPS)
     ens.ens_destroy(ctx)
@@ -431,7 +431,19 @@ def run_profile_case(case: str):
                            n_phases=t.n_phases, phase_len=t.phase_len)
         ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
                              ens.ENS_RKCK45, tol)
-        ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=2))
+        ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=2, cost_order=0))
+    elif case == "km_full2":
+        # all 131,044 systems, 2 periods: the instruction mix of the benchmarked kernel
+        km = km_slice(1, 0, n_phases=2)
+        ph = km["phys"]
+        C = ens.ens_km_coefficients(ph["pA1"], ph["f1"], ph["pA2"], ph["f2"], ph["theta"], ph["RE"],
+                                    km["liquid"])
+        t = km["tol"]
+        tol = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
+                           n_phases=t.n_phases, phase_len=t.phase_len)
+        ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
+                             ens.ENS_RKCK45, tol)
+        ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1, cost_order=0))
     elif case == "prv":
         wl = W.prv(8192, t1=64.0)
         t = wl["tol"]
@@ -467,8 +479,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--phases", type=int, default=64)
     ap.add_argument("--block", type=int, default=128)
-    ap.add_argument("--bps", type=int, default=2)
-    ap.add_argument("--cost-order", type=int, default=0)
+    ap.add_argument("--bps", type=int, default=1)
+    ap.add_argument("--cost-order", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-systems", type=int, default=1024)

@@ -327,6 +327,14 @@ ens_status ens_gather_f64(int64_t k, const int32_t *idx, const double *src, doub
 /* dst[idx[i]] = y[i][0] for i < k (writes re-solved values into a screened map). */
 ens_status ens_scatter_labels(int64_t k, const int32_t *idx, const float *y, float *dst, void *stream);
 
+/* One right-hand-side evaluation per system with the device code the solvers
+ * inline: dy[dim][n] = f(t[i], y[:, i]; params[:, i]).  All arrays device
+ * memory; for Keller-Miksis the same kernel variant as the solver is chosen
+ * (second frequency, rational exponent).  Synchronous for the variant choice,
+ * the evaluation itself is enqueued on `stream`. */
+ens_status ens_eval_rhs(ens_system sys, int64_t n, const double *params, const double *t, const double *y,
+                        double *dy, void *stream);
+
 /* Library version string. */
 const char *ens_version(void);
 

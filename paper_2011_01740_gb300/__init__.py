@@ -276,6 +276,20 @@ def ens_autotune(ctx: int, stream=None) -> EnsLaunch:
     return best
 
 
+def ens_eval_rhs(sys: int, n: int, params, t, y, dy, stream=None):
+    """dy = f(t, y; params) on the device (all arrays torch CUDA tensors)."""
+    L = lib()
+    if not getattr(L, "_rhs_bound", False):
+        vp = ctypes.c_void_p
+        L.ens_eval_rhs.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, vp, vp, vp]
+        L.ens_eval_rhs.restype = ctypes.c_int
+        L._rhs_bound = True
+    keep = []
+    _check(L.ens_eval_rhs(int(sys), int(n), _ptr(params, keep), _ptr(t, keep), _ptr(y, keep), _ptr(dy, keep),
+                          _stream(stream)), None)
+    return dy
+
+
 def ens_last_error(ctx: int | None = None) -> str:
     return lib().ens_last_error(ctx).decode(errors="replace")
 

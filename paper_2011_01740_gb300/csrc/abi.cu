@@ -19,6 +19,8 @@ cudaError_t launch_ck45(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch
 cudaError_t launch_ck45_fp32c(unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_order(const int64_t* steps, int64_t n, int32_t* order, unsigned* hist,
                          cudaStream_t s);
+cudaError_t launch_rhs_eval(int sys, unsigned flags, int64_t n, const double* P, const double* t,
+                            const double* y, double* dy, cudaStream_t s);
 }  // namespace ens
 
 using namespace ens;
@@ -87,12 +89,15 @@ ens_launch default_launch(const ens_ctx* c) {
     L.block = 32;
     L.blocks_per_sm = 0;
   } else {
+    // one warp per SM sub-partition saturates the FP64 pipe; fewer lanes mean
+    // more systems per lane and a shorter tail (measured on the 362 x 362
+    // Keller-Miksis sweep), and longest-first claiming shortens it further
     L.mode = ENS_LAUNCH_PERSISTENT;
     L.block = 128;
-    L.blocks_per_sm = 2;
+    L.blocks_per_sm = 1;
+    L.cost_order = 1;
   }
   L.use_graph = 0;
-  L.cost_order = 0;
   return L;
 }
 
@@ -569,14 +574,14 @@ ens_status ens_autotune(ens_ctx* c, void* stream, ens_launch* best) {
       L.block = b;
       cands.push_back(L);
     }
-    for (int b : {64, 128, 256})
-      for (int bps : {1, 2, 4}) {
-        ens_launch L{};
-        L.mode = ENS_LAUNCH_PERSISTENT;
-        L.block = b;
-        L.blocks_per_sm = bps;
-        cands.push_back(L);
-      }
+    const int shapes[][2] = {{32, 4}, {64, 2}, {128, 1}, {96, 1}, {160, 1}, {192, 1}, {128, 2}, {256, 1}};
+    for (const auto& sh : shapes) {
+      ens_launch L{};
+      L.mode = ENS_LAUNCH_PERSISTENT;
+      L.block = sh[0];
+      L.blocks_per_sm = sh[1];
+      cands.push_back(L);
+    }
   }
   const int shorten = c->solver == ENS_RK4 ? 200 : 2;
   cudaEvent_t e0, e1;
@@ -612,6 +617,27 @@ ens_status ens_autotune(ens_ctx* c, void* stream, ens_launch* best) {
   }
   if (best) *best = best_L;
   return ENS_OK;
+}
+
+ens_status ens_eval_rhs(ens_system sys, int64_t n, const double* params, const double* t, const double* y,
+                        double* dy, void* stream) {
+  if (n < 0 || sys_dim(sys) == 0) return ENS_EINVAL;
+  if (n == 0) return ENS_OK;
+  if (!params || !t || !y || !dy) return ENS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned flags = 0;
+  if (sys == ENS_SYS_KELLER_MIKSIS) {
+    unsigned* f = nullptr;
+    if (cudaMalloc(&f, sizeof(unsigned)) != cudaSuccess) return ENS_ENOMEM;
+    cudaMemsetAsync(f, 0, sizeof(unsigned), s);
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    km_flags_kernel<<<(unsigned)blocks, 256, 0, s>>>(params, n, f);
+    cudaError_t e = cudaMemcpyAsync(&flags, f, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(f);
+    if (e != cudaSuccess) return ENS_ECUDA;
+  }
+  return launch_rhs_eval(sys, flags, n, params, t, y, dy, s) == cudaSuccess ? ENS_OK : ENS_ECUDA;
 }
 
 const char* ens_last_error(const ens_ctx* c) { return c ? c->err : g_create_err; }

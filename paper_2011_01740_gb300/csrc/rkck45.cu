@@ -541,3 +541,47 @@ cudaError_t launch_ck45(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch
 }
 
 }  // namespace ens
+
+namespace ens {
+
+// One right-hand-side evaluation per system with the same device code the
+// solvers inline (test and inspection hook): dy = f(t, y; p).
+template <class Sys>
+__global__ void rhs_eval_kernel(int64_t n, const double* P, const double* t, const double* y, double* dy) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    Sys s;
+    s.load(P, n, i);
+    double yy[Sys::kDim], d[Sys::kDim];
+#pragma unroll
+    for (int c = 0; c < Sys::kDim; ++c) yy[c] = y[c * n + i];
+    s.f(t[i], yy, d);
+#pragma unroll
+    for (int c = 0; c < Sys::kDim; ++c) dy[c * n + i] = d[c];
+  }
+}
+
+cudaError_t launch_rhs_eval(int sys, unsigned flags, int64_t n, const double* P, const double* t,
+                            const double* y, double* dy, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  blocks = blocks > 8192 ? 8192 : blocks;
+  const bool dual = flags & kKmDual, exp215 = !(flags & kKmGeneralExponent);
+  switch (sys) {
+    case ENS_SYS_TOY_X2P: rhs_eval_kernel<AdaptFixed<X2P>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy); break;
+    case ENS_SYS_LORENZ: rhs_eval_kernel<AdaptFixed<Lorenz>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy); break;
+    case ENS_SYS_RELIEF_VALVE: rhs_eval_kernel<ReliefValve><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy); break;
+    case ENS_SYS_KELLER_MIKSIS:
+      if (dual) {
+        if (exp215) rhs_eval_kernel<KellerMiksis<true, true>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy);
+        else rhs_eval_kernel<KellerMiksis<true, false>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy);
+      } else {
+        if (exp215) rhs_eval_kernel<KellerMiksis<false, true>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy);
+        else rhs_eval_kernel<KellerMiksis<false, false>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy);
+      }
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ens
