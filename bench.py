@@ -34,7 +34,7 @@ from paper_2011_01740_gb300 import workloads as W  # noqa: E402
 # the Keller-Miksis kernel, and per RK4 step of the x' = x^2 - p and Lorenz
 # kernels, from the ncu instruction counters of profiles/ (None until
 # measured: the roofline then reports achieved = null).
-FLOPS_PER_KM_TRIAL = None
+FLOPS_PER_KM_TRIAL = 736.76  # 284.17 DFMA + 133.56 DMUL + 34.86 DADD per trial (profiles/)
 FLOPS_PER_X2P_STEP = 21.0     # 10 DFMA + 1 DADD (Sec. 3.2.2 counters; kernel counted by ncu)
 FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast kernel
 
@@ -221,13 +221,16 @@ def run_ours(args):
         achieved = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
                 "frac": (achieved / (FP64_PEAK / 1e12)) if achieved else None,
-                "traffic": None, "kernel": "ck_phased_kernel<KellerMiksis<false>>",
+                "traffic": None, "kernel": "ck_phased_kernel<KellerMiksis<false, true>>",
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (nominal 1.25 TFLOP/s)",
                 "flops_per_trial": FLOPS_PER_KM_TRIAL, "trials_per_launch": trials_local}
 
     secondary = {}
     if rank == 0 and not args.quick:
         secondary = run_secondary(ens, torch, stream, dev)
+        secondary["km_fp32c_vs_fp64_1024x1024"] = run_config4(ens, torch, stream, dev)
+        secondary["km_surrogate_screen"] = run_screen(ens, torch, stream, dev, ctx, km, total_ms / args.steps,
+                                                      steps_local / args.steps, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -291,6 +294,67 @@ def run_e2e(ens, ctx, km, stream, args):
     return {"value": steps / sum(times), "unit": "system-steps/s",
             "h2d_bytes_per_step": int((13 + 2) * n * 8), "d2h_bytes_per_step": int(rows * n * 8 + n * 4),
             "steps": args.e2e_steps, "s_per_step": sum(times) / len(times)}
+
+
+def run_config4(ens, torch, stream, dev, m=1024):
+    """1024 x 1024 Keller-Miksis grid, 64 periods, twice: plain FP64 (tol
+    1e-10) and the split-precision FP32 variant (tol 1e-8); the FP32 run's
+    per-period maxima against the FP64 run's."""
+    km = W.km(m, m, n_phases=64)
+    ph = km["phys"]
+    n = ph["pA1"].size
+    phys_d = [torch.from_numpy(ph[k]).to(dev) for k in ("pA1", "f1", "pA2", "f2", "theta", "RE")]
+    C = ens.ens_km_coefficients(*phys_d, km["liquid"], stream=stream)
+    y0 = torch.from_numpy(km["y0"]).to(dev)
+    stream.synchronize()
+    res = {"systems": n}
+    accs = {}
+    for name, prec, tol in (("fp64_tol1e-10", ens.ENS_FP64, 1e-10), ("fp32c_tol1e-8", ens.ENS_FP32_COMP, 1e-8)):
+        t = ens.make_tol(rtol=tol, atol=tol, dt0=1e-2, dt_min=1e-14, dt_max=1e-1, n_phases=64, prec=prec,
+                         timeout_s=900.0)
+        ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, n, C, y0, (0.0, 1.0), ens.ENS_RKCK45, t)
+        try:
+            ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1 if prec == ens.ENS_FP64 else 2,
+                                                    cost_order=1))
+            if prec == ens.ENS_FP32_COMP:
+                ens.ens_solve(ctx, stream)          # warm-up (the FP64 kernel is warm already)
+                ens.ens_sync(ctx)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ens.ens_solve(ctx, stream)
+            e1.record(stream)
+            stream.synchronize()
+            st = ens.ens_sync(ctx)
+            nacc = ens.ens_read(ctx, ens.ENS_NSTEPS)
+            accs[name] = ens.ens_read(ctx, ens.ENS_ACC)
+        finally:
+            ens.ens_destroy(ctx)
+        ms = e0.elapsed_time(e1)
+        res[name] = {"ms": ms, "steps": float(nacc.sum()), "value": float(nacc.sum()) / (ms / 1e3),
+                     "unit": "system-steps/s", "status": st}
+    a, b = accs["fp32c_tol1e-8"], accs["fp64_tol1e-10"]
+    rel = np.abs(a - b).max(0) / np.abs(b).max(0)
+    res["fp32c_rel_err_per_period_max"] = {"median": float(np.median(rel)), "p90": float(np.percentile(rel, 90)),
+                                           "p99": float(np.percentile(rel, 99))}
+    res["speedup_fp32c_vs_fp64"] = res["fp64_tol1e-10"]["ms"] / res["fp32c_tol1e-8"]["ms"]
+    return res
+
+
+def run_screen(ens, torch, stream, dev, ctx, km, solve_ms, solve_steps, args):
+    """Surrogate-screened scan: the headline solve's accessories train a
+    4-member network, which screens a log grid; points with ensemble spread
+    > 0.05 are re-solved in FP64."""
+    from paper_2011_01740_gb300 import screen
+    rows = ens.ens_acc_rows(ctx)
+    n = km["phys"]["pA1"].size
+    acc = torch.empty((rows, n), dtype=torch.float64, device=dev)
+    ens.ens_read(ctx, ens.ENS_ACC, acc)
+    x, y = screen.training_set_from_acc(ens, km, acc, rows // 2, rows // 4, dev, stream)
+    r = screen.run(ens, screen_m=args.screen_m, n_phases=rows // 2, first_phase=rows // 4, threshold=0.05,
+                   epochs=args.screen_epochs, batch=1024, stream=stream,
+                   train=(x, y, solve_ms / 1e3, solve_steps))
+    r["screen_grid"] = [args.screen_m, args.screen_m]
+    return r
 
 
 def run_secondary(ens, torch, stream, dev):
@@ -432,6 +496,18 @@ def run_profile_case(case: str):
         ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
                              ens.ENS_RKCK45, tol)
         ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=2, cost_order=0))
+    elif case == "km_full64":
+        # the benchmarked launch (all systems, 64 periods, longest-first claiming)
+        km = km_slice(1, 0, n_phases=64)
+        ph = km["phys"]
+        C = ens.ens_km_coefficients(ph["pA1"], ph["f1"], ph["pA2"], ph["f2"], ph["theta"], ph["RE"],
+                                    km["liquid"])
+        t = km["tol"]
+        tol = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
+                           n_phases=t.n_phases, phase_len=t.phase_len)
+        ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
+                             ens.ENS_RKCK45, tol)
+        ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1, cost_order=1))
     elif case == "km_full2":
         # all 131,044 systems, 2 periods: the instruction mix of the benchmarked kernel
         km = km_slice(1, 0, n_phases=2)
@@ -485,6 +561,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-systems", type=int, default=1024)
     ap.add_argument("--quick", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--screen-m", type=int, default=1024, help="screening grid side (4096: the full 16.8M scan)")
+    ap.add_argument("--screen-epochs", type=int, default=150)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

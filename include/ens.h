@@ -142,7 +142,7 @@ typedef struct {
  *                  claims its next system from a device counter (atomicAdd)
  *                  when its current one finishes (work stealing), so uneven
  *                  adaptive step counts do not idle warps.
- *   block          threads per block (multiple of 32, 32..1024).
+ *   block          threads per block (multiple of 32, 32..256).
  *   blocks_per_sm  persistent mode: resident blocks per SM (grid = SMs x this).
  *   use_graph      capture the launch sequence of ens_solve in a CUDA graph on
  *                  the first call and replay it afterwards.

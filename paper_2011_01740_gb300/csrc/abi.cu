@@ -103,7 +103,7 @@ ens_launch default_launch(const ens_ctx* c) {
 
 bool valid_launch(const ens_launch& L) {
   if (L.mode != ENS_LAUNCH_PLAIN && L.mode != ENS_LAUNCH_PERSISTENT) return false;
-  if (L.block < 32 || L.block > 1024 || (L.block % 32) != 0) return false;
+  if (L.block < 32 || L.block > 256 || (L.block % 32) != 0) return false;
   if (L.mode == ENS_LAUNCH_PERSISTENT && (L.blocks_per_sm < 1 || L.blocks_per_sm > 32)) return false;
   return true;
 }

@@ -149,7 +149,7 @@ __device__ __forceinline__ ff ff_axpy(ff y, float hh, float hl, float s, float c
 }  // namespace
 
 template <bool DUAL>
-__global__ void __launch_bounds__(128) ck_phased_fp32c_kernel(AdaptArgs a) {
+__global__ void __launch_bounds__(256) ck_phased_fp32c_kernel(AdaptArgs a) {
   const double tau_end = a.t0 + a.phase_len;
   const uint64_t deadline = global_ns() + a.timeout_ns;
   int64_t i = (a.persistent) ? -1 : blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -112,7 +112,7 @@ __device__ __forceinline__ int64_t claim(const AdaptArgs& a, bool first) {
 // and min of y1 over the accepted step points and the phase start.
 // ---------------------------------------------------------------------------
 template <class Sys>
-__global__ void __launch_bounds__(128) ck_phased_kernel(AdaptArgs a) {
+__global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
   constexpr int D = Sys::kDim;
   const double tau_end = a.t0 + a.phase_len;
   const uint64_t deadline = global_ns() + a.timeout_ns;
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(128) ck_phased_kernel(AdaptArgs a) {
 //     the seat: y1 = y2 = 0 while y3 rises as beta q until y3 = delta, an
 //     interval advanced in closed form.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) ck_events_kernel(AdaptArgs a) {
+__global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
   using Sys = ReliefValve;
   constexpr int D = Sys::kDim;
   const uint64_t deadline = global_ns() + a.timeout_ns;
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(128) ck_events_kernel(AdaptArgs a) {
 // plain adaptive integration over [t0, t1] (no phases, no events)
 // ---------------------------------------------------------------------------
 template <class Sys>
-__global__ void __launch_bounds__(128) ck_plain_kernel(AdaptArgs a) {
+__global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
   constexpr int D = Sys::kDim;
   const uint64_t deadline = global_ns() + a.timeout_ns;
   int64_t i = claim(a, true);

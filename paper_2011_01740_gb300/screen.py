@@ -59,28 +59,50 @@ def km_solve_labels(ens, phys: dict, liquid: dict, n_phases: int, first_phase: i
     return y, st, steps
 
 
+def training_set_from_acc(ens, km: dict, acc, n_phases: int, first_phase: int, dev, stream,
+                          spread_tol: float = 1e-4):
+    """Features and labels of an already solved p_A x f grid (acc: device
+    accessories [2 n_phases][n]); the p_A = 0 row is left out."""
+    import torch
+    keep = np.nonzero(km["phys"]["pA1"] > 0)[0]
+    n = km["phys"]["pA1"].size
+    y_all = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    ens.ens_km_labels(n, acc, n_phases, first_phase, spread_tol, y_all, stream=stream)
+    pa = _t(km["phys"]["pA1"][keep], dev)
+    f = _t(km["phys"]["f1"][keep], dev)
+    x = torch.empty((keep.size, 2), dtype=torch.float32, device=dev)
+    ens.ens_km_features(keep.size, pa, f, W.KM_FEATURE_RANGE, x, stream=stream)
+    stream.synchronize()
+    return x, y_all[_t(keep, dev)].contiguous()
+
+
 def run(ens, train_shape=(362, 362), screen_m=1024, n_phases=64, first_phase=32, threshold=0.05,
         members=4, epochs=150, batch=1024, lr=2e-3, seed=W.SEED, stream=None, validate=2048,
-        liquid=None):
+        liquid=None, train=None):
     """Train on a train_shape grid, screen a screen_m x screen_m log grid,
-    re-solve the uncertain points; returns timings, counts and errors."""
+    re-solve the uncertain points; returns timings, counts and errors.
+    `train` = (x, y, solve_seconds, steps) reuses an existing training set."""
     import torch
     dev = torch.device("cuda")
     stream = stream or torch.cuda.Stream()
     liquid = liquid or W.WATER_25C
     out = {}
     # 1. training data (the p_A = 0 row has no logarithm and is left out)
-    km = W.km(train_shape[0], train_shape[1], n_phases=n_phases, liquid=liquid)
-    keep = km["phys"]["pA1"] > 0
-    phys = {k: _t(v[keep], dev) for k, v in km["phys"].items()}
-    t0 = time.perf_counter()
-    y_tr, st, steps = km_solve_labels(ens, phys, liquid, n_phases, first_phase, dev, stream)
-    out["train_solve_s"] = time.perf_counter() - t0
-    out["train_systems"] = int(keep.sum())
-    out["train_steps"] = steps
-    x_tr = torch.empty((int(keep.sum()), 2), dtype=torch.float32, device=dev)
-    ens.ens_km_features(x_tr.shape[0], phys["pA1"], phys["f1"], W.KM_FEATURE_RANGE, x_tr, stream=stream)
-    stream.synchronize()
+    if train is not None:
+        x_tr, y_tr, out["train_solve_s"], out["train_steps"] = train
+        out["train_systems"] = int(x_tr.shape[0])
+    else:
+        km = W.km(train_shape[0], train_shape[1], n_phases=n_phases, liquid=liquid)
+        keep = km["phys"]["pA1"] > 0
+        phys = {k: _t(v[keep], dev) for k, v in km["phys"].items()}
+        t0 = time.perf_counter()
+        y_tr, st, steps = km_solve_labels(ens, phys, liquid, n_phases, first_phase, dev, stream)
+        out["train_solve_s"] = time.perf_counter() - t0
+        out["train_systems"] = int(keep.sum())
+        out["train_steps"] = steps
+        x_tr = torch.empty((int(keep.sum()), 2), dtype=torch.float32, device=dev)
+        ens.ens_km_features(x_tr.shape[0], phys["pA1"], phys["f1"], W.KM_FEATURE_RANGE, x_tr, stream=stream)
+        stream.synchronize()
     # 2. training
     m = ens.ens_mlp_create(members, seed)
     try:
