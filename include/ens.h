@@ -335,6 +335,44 @@ ens_status ens_scatter_labels(int64_t k, const int32_t *idx, const float *y, flo
 ens_status ens_eval_rhs(ens_system sys, int64_t n, const double *params, const double *t, const double *y,
                         double *dy, void *stream);
 
+/* Allocation-free adaptive solve (the paper has no counterpart: it concerns
+ * how the library is embedded, not the method).
+ *
+ * For callers that cannot allocate device memory themselves or through this
+ * library: processes whose device memory belongs to another allocator (a
+ * framework's caching pool, a preallocated arena of a real-time or embedded
+ * deployment) that must not be bypassed or fragmented, and plugins that are
+ * only handed device buffers by their host.  ens_create allocates; this call
+ * does not.  It runs the same persistent, work-stealing Cash-Karp kernel as
+ * ens_solve (FP64; Keller-Miksis in phase mode, or the relief valve with
+ * events) directly on caller-owned device buffers laid out as ens_read
+ * returns them:
+ *   params [npar][n], y0 [dim][n]                       inputs (not modified)
+ *   y [dim][n], t_out [n], dt_out [n], acc [rows][n],
+ *   status [n] (int32), nacc, nrej, nrhs [n] (int64)    outputs
+ * (rows as ens_acc_rows would give: 2 n_phases, or 35 for the relief valve).
+ * cost_order != 0 claims systems longest first after a one-phase pilot
+ * (written into the output buffers, then overwritten).
+ *
+ * Its only other memory is a fixed ~4.2 MB array in the library's device
+ * globals (claim counter, status OR, claim order): every GPU that loads the
+ * library holds it until the process exits, which caps n at 1,048,576
+ * systems (larger n is ENS_EINVAL with a message in ens_last_error(NULL)).
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with that device current); make it before any
+ * stream capture.  Calls share the array: the counter and the status OR are
+ * cleared at the start of every call, and calls that overlap on the GPU (on
+ * different streams, or from different host threads) race on it.  No call
+ * to cudaMalloc, cudaFree or any allocating routine is made.  Work is
+ * enqueued on `stream` (one small synchronous read selects the
+ * Keller-Miksis kernel variant).  Returns ENS_OK, ENS_EINVAL (arguments, n
+ * above the cap, non-device arrays), ENS_ENOTSUP (other systems or
+ * precisions) or ENS_ECUDA. */
+ens_status ens_solve_noalloc(ens_system sys, int64_t n, const double *params, const double *y0,
+                             const double t_span[2], const ens_tol *tol, double *y, double *t_out,
+                             double *dt_out, double *acc, int32_t *status, int64_t *nacc, int64_t *nrej,
+                             int64_t *nrhs, int32_t cost_order, void *stream);
+
 /* Library version string. */
 const char *ens_version(void);
 

@@ -290,6 +290,25 @@ def ens_eval_rhs(sys: int, n: int, params, t, y, dy, stream=None):
     return dy
 
 
+def ens_solve_noalloc(sys: int, n: int, params, y0, t_span, tol: EnsTol, y, t_out, dt_out, acc, status,
+                      nacc, nrej, nrhs, cost_order: int = 1, stream=None):
+    """Allocation-free solve on caller-owned device buffers (torch CUDA
+    tensors); see ens.h.  For callers that cannot allocate device memory."""
+    L = lib()
+    if not getattr(L, "_noalloc_bound", False):
+        vp = ctypes.c_void_p
+        L.ens_solve_noalloc.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_double * 2,
+                                        ctypes.POINTER(EnsTol)] + [vp] * 8 + [ctypes.c_int32, vp]
+        L.ens_solve_noalloc.restype = ctypes.c_int
+        L._noalloc_bound = True
+    keep = []
+    ts = (ctypes.c_double * 2)(float(t_span[0]), float(t_span[1]))
+    ptrs = [_ptr(a, keep) for a in (params, y0)]
+    outs = [_ptr(a, keep) for a in (y, t_out, dt_out, acc, status, nacc, nrej, nrhs)]
+    _check(L.ens_solve_noalloc(int(sys), int(n), *ptrs, ts, ctypes.byref(tol), *outs, int(cost_order),
+                               _stream(stream)), None)
+
+
 def ens_last_error(ctx: int | None = None) -> str:
     return lib().ens_last_error(ctx).decode(errors="replace")
 

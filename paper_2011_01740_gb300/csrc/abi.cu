@@ -312,6 +312,16 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int sh
 }
 
 std::mutex g_tune_mu;
+
+}  // namespace
+
+namespace ens {
+// Message of a failed call that has no context, returned by ens_last_error(NULL).
+void set_call_error(const char* msg) { set_err(nullptr, "%s", msg); }
+}  // namespace ens
+
+namespace {
+
 std::map<std::tuple<int, int, int, int64_t, int, int>, ens_launch> g_tune_cache;
 
 }  // namespace
