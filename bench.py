@@ -35,6 +35,10 @@ from paper_2011_01740_gb300 import workloads as W  # noqa: E402
 # kernels, from the ncu instruction counters of profiles/ (None until
 # measured: the roofline then reports achieved = null).
 FLOPS_PER_KM_TRIAL = 736.76  # 284.17 DFMA + 133.56 DMUL + 34.86 DADD per trial (profiles/)
+# DRAM bytes (read + write) of one benchmarked Keller-Miksis launch, from the
+# one-pass ncu capture in profiles/ (inputs 15.7 MB read once, 134 MB of
+# per-period accessories written once); None once the kernel changes.
+KM_LAUNCH_DRAM_BYTES = 29225216 + 115527936
 FLOPS_PER_X2P_STEP = 21.0     # 10 DFMA + 1 DADD (Sec. 3.2.2 counters; kernel counted by ncu)
 FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast kernel
 
@@ -221,7 +225,7 @@ def run_ours(args):
         achieved = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
                 "frac": (achieved / (FP64_PEAK / 1e12)) if achieved else None,
-                "traffic": None, "kernel": "ck_phased_kernel<KellerMiksis<false, true>>",
+                "traffic": KM_LAUNCH_DRAM_BYTES, "kernel": "ck_phased_kernel<KellerMiksis<false, true>>",
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (nominal 1.25 TFLOP/s)",
                 "flops_per_trial": FLOPS_PER_KM_TRIAL, "trials_per_launch": trials_local}
 
@@ -520,6 +524,33 @@ def run_profile_case(case: str):
         ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
                              ens.ENS_RKCK45, tol)
         ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1, cost_order=0))
+    elif case == "km_fp32c":
+        km = km_slice(1, 0, n_phases=2)
+        idx = W.subsample(km["phys"]["pA1"].size, 16384)
+        km = W.take(km, idx)
+        ph = km["phys"]
+        C = ens.ens_km_coefficients(ph["pA1"], ph["f1"], ph["pA2"], ph["f2"], ph["theta"], ph["RE"],
+                                    km["liquid"])
+        tol = ens.make_tol(rtol=1e-8, atol=1e-8, dt0=1e-2, dt_min=1e-14, dt_max=1e-1, n_phases=2,
+                           prec=ens.ENS_FP32_COMP)
+        ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
+                             ens.ENS_RKCK45, tol)
+        ens.ens_set_launch(ctx, ens.make_launch(block=256, blocks_per_sm=1, cost_order=0))
+    elif case == "mlp_screen":
+        import torch
+        m = ens.ens_mlp_create(4, W.SEED)
+        pa, f = W.screen_grid(512)
+        n = pa.size
+        x = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+        ens.ens_km_features(n, torch.from_numpy(pa).cuda(), torch.from_numpy(f).cuda(), W.KM_FEATURE_RANGE, x)
+        outs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+        for _ in range(2):
+            ens.ens_mlp_screen(m, n, x, *outs)
+        torch.cuda.synchronize()
+        ens.ens_mlp_destroy(m)
+        print(json.dumps({"case": case, "points": n, "members": 4,
+                          "mac_per_point_member": 49664}), flush=True)
+        return
     elif case == "prv":
         wl = W.prv(8192, t1=64.0)
         t = wl["tol"]
