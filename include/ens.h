@@ -307,6 +307,12 @@ ens_status ens_mlp_train(ens_mlp *m, int64_t n, const float *x, const float *y, 
  * of output 0 over the members), p1[n] (mean sigmoid of output 1). */
 ens_status ens_mlp_screen(ens_mlp *m, int64_t n, const float *x, float *mean, float *stdv, float *p1,
                           void *stream);
+/* Choose the screening kernel: 1 (default) the tcgen05 kernel (accumulators
+ * in tensor memory, one CTA per SM per member), 0 the mma.sync kernel that
+ * fuses all members in one block.  If wait_expired is not NULL it receives
+ * 1 when a tcgen05 launch since the last call gave up waiting for its tensor
+ * cores (its outputs are then invalid), else 0. */
+ens_status ens_mlp_set_screen_impl(ens_mlp *m, int32_t impl, int32_t *wait_expired);
 const char *ens_mlp_last_error(const ens_mlp *m);
 void ens_mlp_destroy(ens_mlp *m);
 

@@ -451,6 +451,19 @@ def ens_mlp_screen(m: int, n: int, x, mean, stdv, p1, stream=None):
                                       _stream(stream)), m)
 
 
+def ens_mlp_set_screen_impl(m: int, impl: int) -> int:
+    """Select the screening kernel (1 tcgen05, 0 mma.sync); returns 1 if a
+    tcgen05 launch since the last call gave up waiting for its tensor cores."""
+    L = _mlp_lib()
+    if not getattr(L, "_impl_bound", False):
+        L.ens_mlp_set_screen_impl.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.ens_mlp_set_screen_impl.restype = ctypes.c_int
+        L._impl_bound = True
+    flag = ctypes.c_int32(0)
+    _mcheck(L.ens_mlp_set_screen_impl(m, int(impl), ctypes.byref(flag)), m)
+    return int(flag.value)
+
+
 def ens_mlp_last_error(m: int | None = None) -> str:
     return _mlp_lib().ens_mlp_last_error(m).decode(errors="replace")
 

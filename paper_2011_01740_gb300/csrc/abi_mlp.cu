@@ -32,6 +32,12 @@ struct ens_mlp {
   float* out = nullptr;
   float* dout = nullptr;
   float* loss = nullptr;          // [members]
+  // screening on the tcgen05 tensor cores
+  int screen_impl = 1;            // 1: tcgen05 kernel, 0: mma.sync fused kernel
+  float* screen_out = nullptr;    // [members][screen_cap][2]
+  int64_t screen_cap = 0;
+  unsigned* screen_err = nullptr;
+  int sms = 0;
   char err[512] = {0};
 };
 
@@ -433,6 +439,26 @@ ens_status ens_mlp_screen(ens_mlp* m, int64_t n, const float* x, float* mean, fl
     merr(m, "ens_mlp_screen: arrays must be device memory");
     return ENS_EINVAL;
   }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m->screen_impl == 1) {
+    if (n > m->screen_cap) {
+      cudaFree(m->screen_out);
+      m->screen_out = nullptr;
+      m->screen_cap = 0;
+      MLP_CUDA(m, cudaMalloc(&m->screen_out, (size_t)m->members * n * 2 * sizeof(float)));
+      m->screen_cap = n;
+    }
+    if (!m->screen_err) MLP_CUDA(m, cudaMalloc(&m->screen_err, sizeof(unsigned)));
+    if (!m->sms) {
+      int dev = 0;
+      MLP_CUDA(m, cudaGetDevice(&dev));
+      MLP_CUDA(m, cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    MLP_CUDA(m, cudaMemsetAsync(m->screen_err, 0, sizeof(unsigned), s));
+    MLP_CUDA(m, mlp::launch_screen_tc05(n, m->members, x, m->master, m->wbf, m->screen_out, m->screen_err, mean,
+                                        stdv, p1, m->sms, s));
+    return ENS_OK;
+  }
   mlp::FwdArgs f{};
   f.n = n;
   f.members = m->members;
@@ -442,7 +468,18 @@ ens_status ens_mlp_screen(ens_mlp* m, int64_t n, const float* x, float* mean, fl
   f.mean = mean;
   f.stdv = stdv;
   f.p1 = p1;
-  MLP_CUDA(m, mlp::launch_forward_screen(f, (cudaStream_t)stream));
+  MLP_CUDA(m, mlp::launch_forward_screen(f, s));
+  return ENS_OK;
+}
+
+ens_status ens_mlp_set_screen_impl(ens_mlp* m, int32_t impl, int32_t* wait_expired) {
+  if (!m || (impl != 0 && impl != 1)) return ENS_EINVAL;
+  if (wait_expired) {
+    unsigned e = 0;
+    if (m->screen_err) MLP_CUDA(m, cudaMemcpy(&e, m->screen_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    *wait_expired = (int32_t)e;
+  }
+  m->screen_impl = impl;
   return ENS_OK;
 }
 
@@ -462,6 +499,8 @@ void ens_mlp_destroy(ens_mlp* m) {
   cudaFree(m->dz);
   cudaFree(m->out);
   cudaFree(m->dout);
+  cudaFree(m->screen_out);
+  cudaFree(m->screen_err);
   delete m;
 }
 

@@ -8,7 +8,9 @@
 //          increments added to it, so rounding does not accumulate over the
 //          ~10^5 steps of a run;
 //   FP64   the phase-local time tau, the step h and its proposal, the
-//          acceptance test |err_i| <= atol + rtol max(|y_i|, |y5_i|).
+//          acceptance test |err_i| <= atol + rtol max(|y_i|, |y5_i|)
+//          (err_i and the scale come from float quantities; the comparison
+//          and the tolerances are double).
 // The step factor 0.9 E^(-1/5) only scales the next proposal and is formed
 // in FP32.
 //
@@ -168,6 +170,7 @@ __global__ void __launch_bounds__(256) ck_phased_fp32c_kernel(AdaptArgs a) {
   ff ymax{0.f, 0.f}, ymin{0.f, 0.f};
   int32_t ph = 0, st = 0;
   uint32_t trials = 0, nacc = 0, nrej = 0, nrhs = 0, iter = 0;
+  const float rtol_f = (float)a.rtol, atol_f = (float)a.atol;
 
   auto start_system = [&](int64_t sys) {
     s.load(a.params, a.n, sys);
@@ -276,13 +279,17 @@ __global__ void __launch_bounds__(256) ck_phased_fp32c_kernel(AdaptArgs a) {
       ev.add(D1, k1v); ev.add(D3, k3v); ev.add(D4, k4v); ev.add(D5, k5v); ev.add(D6, k6v);
       const ff n0 = ff_axpy(y0v, hh, hl, bx.s, bx.c);
       const ff n1 = ff_axpy(y1v, hh, hl, bv.s, bv.c);
-      // acceptance in FP64: |err_i| <= atol + rtol max(|y_i|, |y5_i|)
-      const double e0 = fabs(h * (double)ex.value()), e1 = fabs(h * (double)ev.value());
-      const double sc0 = fma(a.rtol, fmax(fabs(ff_to_d(y0v)), fabs(ff_to_d(n0))), a.atol);
-      const double sc1 = fma(a.rtol, fmax(fabs(ff_to_d(y1v)), fabs(ff_to_d(n1))), a.atol);
+      // acceptance in FP64: |err_i| <= atol + rtol max(|y_i|, |y5_i|).  err_i
+      // is a float quantity and the scale needs only the leading (hi) parts of
+      // the states, so ten FP64 instructions decide the step.
+      const float exv = ex.value(), evv = ev.value();
+      const float m0 = fmaxf(fabsf(y0v.hi), fabsf(n0.hi)), m1 = fmaxf(fabsf(y1v.hi), fabsf(n1.hi));
+      const double e0 = fabs(h * (double)exv), e1 = fabs(h * (double)evv);
+      const double sc0 = fma(a.rtol, (double)m0, a.atol), sc1 = fma(a.rtol, (double)m1, a.atol);
       const bool accept = (e0 <= sc0) && (e1 <= sc1);
       // step factor from the float ratio E = max_i |err_i| / sc_i
-      const float E = fmaxf(__fdividef((float)e0, (float)sc0), __fdividef((float)e1, (float)sc1));
+      const float E = fmaxf(__fdividef(fabsf(hh * exv), fmaf(rtol_f, m0, atol_f)),
+                            __fdividef(fabsf(hh * evv), fmaf(rtol_f, m1, atol_f)));
       float fac;
       if (isnan(E)) {
         fac = 0.2f;

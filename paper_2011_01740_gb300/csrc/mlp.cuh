@@ -80,6 +80,12 @@ cudaError_t launch_init(int members, uint64_t seed, float* w, cudaStream_t s);
 cudaError_t launch_gather(int64_t n, const int32_t* idx, const float* x, const float* y, float* xb, float* yb,
                           cudaStream_t s);
 
+// tcgen05 screening forward (mlp_tc05.cu): per-member outputs into out
+// [members][n][2], then mean / spread / period-1 probability.
+cudaError_t launch_screen_tc05(int64_t n, int members, const float* x, const float* master, const __nv_bfloat16* wbf,
+                               float* out, unsigned* error, float* mean, float* stdv, float* p1, int sms,
+                               cudaStream_t s);
+
 // splitmix64 (Steele, Lea & Flood 2014): counter-based generator of the
 // initial weights and of the shuffles.
 __host__ __device__ inline uint64_t splitmix64(uint64_t x) {

@@ -95,25 +95,60 @@ def test_gradient_matches_oracle():
             assert err < BF16_TOL, (k, name, err)
 
 
-def test_screen_agrees_with_member_outputs():
+@pytest.mark.parametrize("impl", [1, 0])
+def test_screen_agrees_with_member_outputs(impl):
+    """Screening (impl 1: tcgen05 kernel with TMEM accumulators, 0: fused
+    mma.sync kernel) against the per-member forward outputs and against the
+    float64 oracle."""
     import torch
     M, n = 4, 5000
     p = W.mlp_params(M)
     x, _ = W.mlp_batch(n, seed=7)
     m = _model(M, p)
     try:
+        ens.ens_mlp_set_screen_impl(m, impl)
         xd = _dev(x)
         out = torch.empty((M, n, 2), dtype=torch.float32, device="cuda")
         ens.ens_mlp_forward(m, n, xd, out)
         mean, sd, p1 = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
         ens.ens_mlp_screen(m, n, xd, mean, sd, p1)
         torch.cuda.synchronize()
+        assert ens.ens_mlp_set_screen_impl(m, impl) == 0          # no expired tensor-core wait
     finally:
         ens.ens_mlp_destroy(m)
     o = out.cpu().numpy().astype(np.float64)
-    np.testing.assert_allclose(mean.cpu().numpy(), o[:, :, 0].mean(0), rtol=1e-5, atol=1e-6)
-    np.testing.assert_allclose(sd.cpu().numpy(), o[:, :, 0].std(0), rtol=1e-4, atol=1e-5)
-    np.testing.assert_allclose(p1.cpu().numpy(), (1 / (1 + np.exp(-o[:, :, 1]))).mean(0), rtol=1e-5, atol=1e-6)
+    exact = dict(rtol=1e-5, atol=1e-6) if impl == 0 else dict(rtol=2e-2, atol=2e-2)
+    np.testing.assert_allclose(mean.cpu().numpy(), o[:, :, 0].mean(0), **exact)
+    np.testing.assert_allclose(sd.cpu().numpy(), o[:, :, 0].std(0), rtol=1e-4 if impl == 0 else 5e-2,
+                               atol=1e-5 if impl == 0 else 2e-2)
+    np.testing.assert_allclose(p1.cpu().numpy(), (1 / (1 + np.exp(-o[:, :, 1]))).mean(0), **exact)
+    refs = np.stack([omlp.forward(p[k].astype(np.float64), x.astype(np.float64))[0] for k in range(M)])
+    ref_mean = refs[:, :, 0].mean(0)
+    err = np.abs(mean.cpu().numpy() - ref_mean).max() / np.abs(ref_mean).max()
+    assert err < BF16_TOL, err
+
+
+def test_screen_tcgen05_large_grid_matches_mma_sync():
+    """Many tiles per CTA (persistent walk) and a ragged last tile."""
+    import torch
+    M, n = 4, 300_001
+    p = W.mlp_params(M, seed=5)
+    x, _ = W.mlp_batch(n, seed=9)
+    m = _model(M, p)
+    try:
+        xd = _dev(x)
+        res = {}
+        for impl in (1, 0):
+            ens.ens_mlp_set_screen_impl(m, impl)
+            outs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+            ens.ens_mlp_screen(m, n, xd, *outs)
+            torch.cuda.synchronize()
+            res[impl] = [o.cpu().numpy() for o in outs]
+        assert ens.ens_mlp_set_screen_impl(m, 1) == 0
+    finally:
+        ens.ens_mlp_destroy(m)
+    for a, b in zip(res[1], res[0]):
+        np.testing.assert_allclose(a, b, rtol=2e-2, atol=2e-2)
 
 
 def test_training_reduces_loss():
