@@ -150,6 +150,7 @@ def run(ens, train_shape=(362, 362), screen_m=1024, n_phases=64, first_phase=32,
     out["fallback_points"] = int(k)
     out["fallback_fraction"] = k / n
     out["fallback_steps"] = fb_steps
+    out["screened_total_s"] = out["screen_s"] + out["fallback_s"]
     # 5. error of the merged map on a validation sample solved in FP64
     if validate:
         vi = W.subsample(n, validate, seed=seed + 7)
@@ -177,6 +178,5 @@ def run(ens, train_shape=(362, 362), screen_m=1024, n_phases=64, first_phase=32,
         # fully occupied training solve
         rate = out["train_steps"] / out["train_solve_s"]
         out["fp64_full_grid_estimate_s"] = (v_steps / vi.size) * n / rate
-        out["screened_total_s"] = out["screen_s"] + out["fallback_s"]
         out["speedup_vs_fp64_estimate"] = out["fp64_full_grid_estimate_s"] / out["screened_total_s"]
     return out
