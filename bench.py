@@ -34,11 +34,14 @@ from paper_2011_01740_gb300 import workloads as W  # noqa: E402
 # the Keller-Miksis kernel, and per RK4 step of the x' = x^2 - p and Lorenz
 # kernels, from the ncu instruction counters of profiles/ (None until
 # measured: the roofline then reports achieved = null).
-FLOPS_PER_KM_TRIAL = 736.76  # 284.17 DFMA + 133.56 DMUL + 34.86 DADD per trial (profiles/)
+FLOPS_PER_KM_TRIAL = 627.84  # 239.64 DFMA + 129.65 DMUL + 18.91 DADD per trial (profiles/)
+# all FP64 thread instructions per trial (DFMA, DMUL, DADD, compares, min/max),
+# for the FP64 pipe's instruction-issue fraction
+FP64_INST_PER_KM_TRIAL = 406.08
 # DRAM bytes (read + write) of one benchmarked Keller-Miksis launch, from the
 # one-pass ncu capture in profiles/ (inputs 15.7 MB read once, 134 MB of
 # per-period accessories written once); None once the kernel changes.
-KM_LAUNCH_DRAM_BYTES = 29225216 + 115527936
+KM_LAUNCH_DRAM_BYTES = 40835840 + 122835968
 FLOPS_PER_X2P_STEP = 21.0     # 10 DFMA + 1 DADD (Sec. 3.2.2 counters; kernel counted by ncu)
 FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast kernel
 
@@ -48,6 +51,7 @@ SMS = 152
 FP64_FLOP_PER_CLK_SM = 4.0
 SM_MAX_MHZ = 2070.0
 FP64_PEAK = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6
+FP64_INST_PEAK = SMS * 2.0 * SM_MAX_MHZ * 1e6   # FP64 thread instructions per second
 
 WORKLOAD = "keller_miksis_362x362_pA0-2bar_f20k-1M_log_64periods_ck45_tol1e-10_fp64"
 METRIC = "accepted RK system-steps/s (Keller-Miksis 362x362 p_A x f grid, Cash-Karp 1e-10, 64 periods, FP64)"
@@ -180,6 +184,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
+    kernel_ms_steps = []
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             with torch.cuda.stream(stream):
@@ -187,6 +192,13 @@ def run_ours(args):
             ev[k][0].record(stream)
             ens.ens_solve(ctx, stream)
             ev[k][1].record(stream)
+            # the main kernel's own events (recorded by the library on this
+            # stream) are read before the next solve records them again
+            stream.synchronize()
+            try:
+                kernel_ms_steps.append(ens.ens_kernel_ms(ctx))
+            except ens.EnsError:
+                kernel_ms_steps.append(None)
         stream.synchronize()
     torch.cuda.synchronize()
     barrier()
@@ -218,7 +230,10 @@ def run_ours(args):
         e2e = run_e2e(ens, ctx, km, stream, args)
 
     # ---- roofline of the dominant kernel ----
-    kernel_ms = total_ms / args.steps
+    if all(k is not None for k in kernel_ms_steps):
+        kernel_ms, kernel_src = float(np.mean(kernel_ms_steps)), "main-kernel CUDA events (ens_kernel_ms)"
+    else:
+        kernel_ms, kernel_src = total_ms / args.steps, "whole solve (pilot and ordering included)"
     if FLOPS_PER_KM_TRIAL is not None:
         achieved = FLOPS_PER_KM_TRIAL * trials_local / (kernel_ms / 1e3) / 1e12
     else:
@@ -227,7 +242,11 @@ def run_ours(args):
                 "frac": (achieved / (FP64_PEAK / 1e12)) if achieved else None,
                 "traffic": KM_LAUNCH_DRAM_BYTES, "kernel": "ck_phased_kernel<KellerMiksis<false, true>>",
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (nominal 1.25 TFLOP/s)",
-                "flops_per_trial": FLOPS_PER_KM_TRIAL, "trials_per_launch": trials_local}
+                "flops_per_trial": FLOPS_PER_KM_TRIAL, "trials_per_launch": trials_local,
+                "kernel_ms": kernel_ms, "duration_source": kernel_src,
+                "fp64_inst_per_trial": FP64_INST_PER_KM_TRIAL,
+                "fp64_issue_frac": (FP64_INST_PER_KM_TRIAL * trials_local / (kernel_ms / 1e3) / FP64_INST_PEAK
+                                    if FP64_INST_PER_KM_TRIAL else None)}
 
     secondary = {}
     if rank == 0 and not args.quick:
@@ -410,7 +429,8 @@ def run_secondary(ens, torch, stream, dev):
                        event_tol=t.event_tol, acc_t_start=t.acc_t_start, timeout_s=900.0)
     ctx = ens.ens_create(ens.ENS_SYS_RELIEF_VALVE, 262144, wl["params"], wl["y0"], (t.t0, t.t1),
                          ens.ENS_RKCK45, tol)
-    ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1, use_graph=1, cost_order=1))
+    # 8 warps per SM measured fastest for the valves (128: 19.0 s, 160/192: 18.1 s, 256: 18.0 s)
+    ens.ens_set_launch(ctx, ens.make_launch(block=256, blocks_per_sm=1, use_graph=1, cost_order=1))
     ms = timed(ctx, 1)
     nacc = ens.ens_read(ctx, ens.ENS_NSTEPS)
     ens.ens_destroy(ctx)
@@ -516,7 +536,7 @@ def run_profile_case(case: str):
                            n_phases=t.n_phases, phase_len=t.phase_len)
         ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
                              ens.ENS_RKCK45, tol)
-        ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1, cost_order=1))
+        ens.ens_set_launch(ctx, ens.make_launch(block=160, blocks_per_sm=1, cost_order=1))
     elif case == "km_full2":
         # all 131,044 systems, 2 periods: the instruction mix of the benchmarked kernel
         km = km_slice(1, 0, n_phases=2)
@@ -528,7 +548,7 @@ def run_profile_case(case: str):
                            n_phases=t.n_phases, phase_len=t.phase_len)
         ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
                              ens.ENS_RKCK45, tol)
-        ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1, cost_order=0))
+        ens.ens_set_launch(ctx, ens.make_launch(block=160, blocks_per_sm=1, cost_order=0))
     elif case == "km_fp32c":
         km = km_slice(1, 0, n_phases=2)
         idx = W.subsample(km["phys"]["pA1"].size, 16384)
@@ -590,7 +610,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--phases", type=int, default=64)
-    ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--block", type=int, default=160)
     ap.add_argument("--bps", type=int, default=1)
     ap.add_argument("--cost-order", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)

@@ -201,6 +201,16 @@ ens_status ens_solve(ens_ctx *ctx, void *stream);
  * another status bit, or ENS_ECUDA. */
 ens_status ens_sync(ens_ctx *ctx);
 
+/* Device time in milliseconds of the main solve kernel of the context's last
+ * solve (CUDA events recorded on the solve's stream right before and after
+ * that launch, also when the solve replays a CUDA graph).  It excludes the
+ * planning work that ens_solve may run first (the one-phase pilot and the
+ * claim-order sort of cost_order).  The paper has no counterpart: a
+ * measurement hook for the kernel-level roofline.  Call after ens_sync;
+ * ENS_EINVAL before the first solve, ENS_ECUDA if the events are not
+ * complete. */
+ens_status ens_kernel_ms(ens_ctx *ctx, double *ms);
+
 /* Copy one output (selector ENS_*) into dst (host or device), which must hold
  * at least the size the selector's layout gives; dst_bytes smaller than that
  * is ENS_EINVAL.  Synchronous with respect to the context's last stream. */

@@ -310,8 +310,9 @@ void orc_rk4_solve(int sys, int64_t n, const double *params, double *y, double t
 {
     const int dim = orc_dim(sys), npar = orc_npar(sys);
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 64)
+    /* a per-call thread count that leaves the process-wide default alone */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
 #endif
     for (int64_t i = 0; i < n; ++i) {
         double p[16], yy[ORC_MAXDIM], yn[ORC_MAXDIM];
@@ -523,10 +524,13 @@ static void solve_phased(int sys, const double *p, int dim, double *y, double *d
  * passes the error test, with g0 = g(t) and g1 = g(t+h):
  *   - overshoot: the impact overshoots when g1 < -tol; the maximum overshoots
  *     when g0 > tol and g1 < -tol.  The trial is thrown away and retried with
- *     the step shortened by the secant (linear interpolation) fraction
- *     g0 / (g0 - g1) of the earliest overshooting event (one half when the
- *     impact starts within the band, g0 <= tol, e.g. right after a bounce);
- *     at most 40 retries in a row.
+ *     the step shortened to the earliest overshooting event's estimated
+ *     root (one half of the step when the impact starts within the band,
+ *     g0 <= tol, e.g. right after a bounce); at most 40 retries in a row.
+ *     The root estimate (event_frac) is the root in (0, h) of the quadratic
+ *     in s that takes the value g0 with slope g'(t) at s = 0 (g' = y2 for
+ *     the impact and y2' for the maximum, both from k1 = f(t, y)) and the
+ *     value g1 at s = h.
  *   - location: otherwise the trial is accepted, and at its end point the
  *     maximum is located when g0 > tol and |g1| <= tol, the impact when
  *     |g1| <= tol and y2 < 0.  Maximum: y1 is appended to the ring of the last
@@ -544,6 +548,28 @@ static void solve_phased(int sys, const double *p, int dim, double *y, double *d
  * row 34 the number of impacts.                                              */
 #define ORC_RING 32
 #define ORC_EV_RETRIES 40
+
+/* Fraction of the trial step at the estimated root of a falling event
+ * function with g0 > 0 at its start (slope d0) and g1 < 0 at its end.
+ * With B = d0 h and A = g1 - g0 - B the model g0 + B x + A x^2 (x = s/h)
+ * changes sign once on (0, 1); its root there is 2 g0 / (-B + sqrt(B^2 -
+ * 4 A g0)) whatever the sign of A (for A > 0 the smaller of two positive
+ * roots, for A < 0 the positive one).  The chord fraction g0 / (g0 - g1)
+ * stands in if rounding takes the quadratic's root out of (0, 1).  The
+ * quadratic is exact for a constant second derivative, so a retry lands in
+ * the band even at a grazing impact, where the chord from the fixed start
+ * point of the retried step closes in only linearly.                        */
+static double event_frac(double g0, double d0, double g1, double h)
+{
+    const double B = d0 * h;
+    const double A = g1 - g0 - B;
+    const double D = B * B - 4.0 * A * g0;
+    const double chord = g0 / (g0 - g1);
+    if (!(D >= 0.0)) return chord;
+    const double den = -B + sqrt(D);
+    const double x = 2.0 * g0 / den;
+    return (den > 0.0 && x > 0.0 && x < 1.0) ? x : chord;
+}
 static void solve_events(int sys, const double *p, int dim, double *y, double *t_io,
                          double *dt_io, const orc_tol *tol, int64_t n, int64_t i, double *acc,
                          int32_t *status, int64_t *nacc, int64_t *nrej, int64_t *nrhs)
@@ -598,12 +624,12 @@ static void solve_events(int sys, const double *p, int dim, double *y, double *t
         }
         /* overshoot test on the error-accepted trial */
         if (y5[0] < -etol) {                                   /* impact */
-            const double frac = (y[0] > etol) ? y[0] / (y[0] - y5[0]) : 0.5;
+            const double frac = (y[0] > etol) ? event_frac(y[0], k1[0], y5[0], h) : 0.5;
             if (frac < best_frac) best_frac = frac;
             overshoot = 1;
         }
         if (y[1] > etol && y5[1] < -etol) {                    /* maximum */
-            const double frac = y[1] / (y[1] - y5[1]);
+            const double frac = event_frac(y[1], k1[1], y5[1], h);
             if (frac < best_frac) best_frac = frac;
             overshoot = 1;
         }
@@ -670,8 +696,9 @@ void orc_cashkarp_solve(int sys, int64_t n, const double *params, double *y, con
 {
     const int dim = orc_dim(sys), npar = orc_npar(sys);
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
+    /* a per-call thread count that leaves the process-wide default alone */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
 #endif
     for (int64_t i = 0; i < n; ++i) {
         double p[16], yy[ORC_MAXDIM];

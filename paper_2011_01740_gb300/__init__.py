@@ -101,6 +101,8 @@ def lib() -> ctypes.CDLL:
         L.ens_solve.restype = st
         L.ens_sync.argtypes = [vp]
         L.ens_sync.restype = st
+        L.ens_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.ens_kernel_ms.restype = st
         L.ens_read.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t]
         L.ens_read.restype = st
         L.ens_acc_rows.argtypes = [vp]
@@ -232,6 +234,13 @@ def ens_sync(ctx: int, raise_on_system: bool = False) -> int:
         return st
     _check(st, ctx)
     return st
+
+
+def ens_kernel_ms(ctx: int) -> float:
+    """Device milliseconds of the last solve's main kernel (after ens_sync)."""
+    ms = ctypes.c_double(0.0)
+    _check(lib().ens_kernel_ms(ctx, ctypes.byref(ms)), ctx)
+    return ms.value
 
 
 _READ_DTYPE = {ENS_STATE: np.float64, ENS_ACC: np.float64, ENS_STATUS: np.int32,

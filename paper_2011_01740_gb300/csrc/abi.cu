@@ -56,6 +56,9 @@ struct ens_ctx {
   cudaStream_t graph_stream = nullptr;
   bool graph_valid = false;
   cudaStream_t last_stream = nullptr;
+  // events around the main solve kernel of the last solve (ens_kernel_ms)
+  cudaEvent_t kev[2] = {nullptr, nullptr};
+  bool kev_recorded = false;
   char err[512] = {0};
 };
 
@@ -89,11 +92,13 @@ ens_launch default_launch(const ens_ctx* c) {
     L.block = 32;
     L.blocks_per_sm = 0;
   } else {
-    // one warp per SM sub-partition saturates the FP64 pipe; fewer lanes mean
-    // more systems per lane and a shorter tail (measured on the 362 x 362
-    // Keller-Miksis sweep), and longest-first claiming shortens it further
+    // about one warp per SM sub-partition saturates the FP64 pipe.  More warps
+    // share the pipe and lengthen the critical path of the longest system
+    // (each warp then advances more slowly); fewer leave the pipe idle on
+    // dependent-instruction latency.  Five warps per SM measured fastest on
+    // the 362 x 362 Keller-Miksis sweep, with longest-first claiming.
     L.mode = ENS_LAUNCH_PERSISTENT;
-    L.block = 128;
+    L.block = 160;
     L.blocks_per_sm = 1;
     L.cost_order = 1;
   }
@@ -131,6 +136,21 @@ void free_buffers(ens_ctx* c) {
   cudaFree(c->scratch);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   c->gexec = nullptr;
+  for (cudaEvent_t& e : c->kev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+}
+
+// Record one of the main-kernel timing events on s.  Inside a stream capture
+// the record becomes an event node of the graph (external record), so every
+// replay of the graph records it again.
+cudaError_t record_kernel_event(ens_ctx* c, int which, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(c->kev[which], s, cudaEventRecordExternal)
+                                             : cudaEventRecord(c->kev[which], s);
 }
 
 // Keller-Miksis kernel selection: bit kKmDual if any system drives with a
@@ -278,8 +298,11 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int sh
     a.t0 = c->t0;
     a.dt = c->tol.dt0;
     a.nsteps = shorten > 0 ? std::min<int64_t>(c->tol.n_steps, shorten) : c->tol.n_steps;
+    ENS_CUDA(c, record_kernel_event(c, 0, s));
     cudaError_t e = launch_rk4(c->sys, c->tol.prec == ENS_FP64_STRICT, a, L.block, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "rk4 launch");
+    ENS_CUDA(c, record_kernel_event(c, 1, s));
+    c->kev_recorded = true;
     return ENS_OK;
   }
   AdaptArgs a = adapt_args(c);
@@ -305,9 +328,12 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int sh
     a.order = c->order;
   }
   AdaptLaunch AL = adapt_launch(c, L);
+  ENS_CUDA(c, record_kernel_event(c, 0, s));
   cudaError_t e = c->tol.prec == ENS_FP32_COMP ? launch_ck45_fp32c(c->km_flags, a, AL, s)
                                                : launch_ck45(c->sys, c->km_flags, a, AL, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "adaptive launch");
+  ENS_CUDA(c, record_kernel_event(c, 1, s));
+  c->kev_recorded = true;
   return ENS_OK;
 }
 
@@ -389,6 +415,8 @@ ens_status ens_create(ens_ctx** out, ens_system sys, int64_t n, const double* pa
   if (e == cudaSuccess) e = dalloc(&c->order, nn);
   if (e == cudaSuccess) e = dalloc(&c->hist, 512);
   if (e == cudaSuccess) e = dalloc(&c->scratch, 1);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->kev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->kev[1]);
   if (e != cudaSuccess) {
     set_err(nullptr, "device allocation: %s", cudaGetErrorString(e));
     free_buffers(c);
@@ -516,6 +544,19 @@ ens_status ens_sync(ens_ctx* c) {
     set_err(c, "some systems finished with status bits 0x%x", any);
     return ENS_ESYSTEM;
   }
+  return ENS_OK;
+}
+
+ens_status ens_kernel_ms(ens_ctx* c, double* ms) {
+  if (!c || !ms) return ENS_EINVAL;
+  *ms = 0.0;
+  if (!c->kev_recorded) {
+    set_err(c, "no solve kernel has been enqueued on this context");
+    return ENS_EINVAL;
+  }
+  float f = 0.0f;
+  ENS_CUDA(c, cudaEventElapsedTime(&f, c->kev[0], c->kev[1]));
+  *ms = (double)f;
   return ENS_OK;
 }
 

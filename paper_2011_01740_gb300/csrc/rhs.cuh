@@ -62,64 +62,102 @@ struct Lorenz {
   }
 };
 
-// x^(-1/5) for a positive double inside the float range.  Float seed from the
-// hardware base-2 logarithm and exponential (PTX lg2.approx / ex2.approx,
-// about 22 correct bits), then one third-order step of the binomial series
-// of (1 - r)^(-1/5) with the residual r = 1 - x v^5:
+// Exact reinterpretation between a positive double and a float with the same
+// exponent, done on the integer pipe (a double <-> float conversion
+// instruction costs about one FP64 pipe slot on this part).  The exponent is
+// rebiased (1023 -> 127) and the significand truncated to 23 bits, so the
+// float is within 2^-23 relative of x; valid for 2^-126 <= x < 2^128.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  return __uint_as_float(((hi - ((1023u - 127u) << 20)) << 3) | (lo >> 29));
+}
+// The inverse, exact for positive normal floats.
+__device__ __forceinline__ double f32_to_f64(float v) {
+  const unsigned b = __float_as_uint(v);
+  return __hiloint2double((int)((b >> 3) + ((1023u - 127u) << 20)), (int)(b << 29));
+}
+
+// x^(-1/5) for 2^-126 <= x < 2^128 (NaN for x <= 0, as pow() gives for the
+// negative bases it is used on).  Float seed from the hardware base-2
+// logarithm and exponential (PTX lg2.approx / ex2.approx, about 22 correct
+// bits, on the integer-reinterpreted float of x), then one third-order step
+// of the binomial series of (1 - r)^(-1/5) with the residual r = 1 - x v^5:
 //   v <- v (1 + r / 5 + 3 r^2 / 25).
-// The neglected r^3 term is below 2^-60 for the seed's accuracy, so the result
-// is within about 2 ulp of x^(-1/5).  Cost: 7 FP64 instructions and two
-// conversions, against roughly a hundred FP64 instructions for pow().
+// The neglected r^3 term (11 r^3 / 125) is below 2^-58 for the seed's
+// accuracy, so the result is within about 2 ulp of x^(-1/5).  Cost: 7 FP64
+// instructions, against roughly a hundred for pow().
 __device__ __forceinline__ double inv_fifth_root(double x) {
-  const float xf = __double2float_rn(x);
+  const float xf = f64_to_f32_trunc(x);
   float l, vf;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(xf));
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(vf) : "f"(-0.2f * l));
-  const double v = (double)vf;
+  const double v = f32_to_f64(vf);
   const double v2 = v * v;
   const double r = fma(-x, (v2 * v2) * v, 1.0);
-  return fma(v * fma(0.12, r, 0.2), r, v);
+  const double res = fma(v * fma(0.12, r, 0.2), r, v);
+  return __double2hiint(x) > 0 ? res : __longlong_as_double(0x7ff8000000000000LL);
 }
 
-// sin(pi x) and cos(pi x) together for |x| < 2^50.  The argument is split
-// exactly as x = k/2 + r with k = nearest integer to 2x and |r| <= 1/4 (the
-// rounding to an integer uses the 1.5 * 2^52 shift, which also leaves k in
-// the low bits); sin(pi r) and cos(pi r) come from their Maclaurin series
-// (coefficients (-1)^j pi^n / n!, n = 2j+1 and 2j) truncated where the next
-// term is below 1e-17 on |r| <= 1/4; k mod 4 quarter turns then select and
-// negate.  22 FP64 instructions, against about 32 for sincospi().
-__device__ __forceinline__ void sincospi_poly(double x, double* sn, double* cs) {
+// 1/d to about 1 ulp: the hardware reciprocal approximation (PTX
+// rcp.approx.ftz.f64, on the leading bits of d) refined by one cubic
+// Newton-Raphson step, v (1 + e + e^2) with e = 1 - d v, which cubes the
+// seed's relative error.  Not correctly rounded; 3 FP64 instructions after
+// the seed.  Zero, infinite and subnormal d give NaN or garbage: callers use it
+// on values bounded away from those.
+__device__ __forceinline__ double rcp_nr(double d) {
+  double v;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(v) : "d"(d));
+  const double e = fma(-d, v, 1.0);
+  return fma(fma(e, e, e), v, v);
+}
+
+// sin(2 pi x) and cos(2 pi x) together for |x| < 2^49.  The argument is split
+// exactly as x = k/4 + r with k the nearest integer to 4x and |r| <= 1/8 (the
+// rounding to an integer uses the 1.5 * 2^52 shift, which leaves k in the low
+// bits; x - k/4 is exact); sin(2 pi r) = r P(r^2) and cos(2 pi r) =
+// 1 + r^2 Q(r^2) with P, Q of degree 6 from a weighted minimax fit (Remez
+// exchange) on r^2 in [0, 1/64]: relative error of P below 5e-17 and absolute
+// error of 1 + r^2 Q below 2e-17 after rounding the coefficients to double
+// (`gen_sincos2pi.py` next to this file recomputes them).  The k mod 4
+// quarter turns then select and negate (the sign flips are integer XORs on
+// the high word).  18 FP64 instructions.
+__device__ __forceinline__ void sincos2pi_poly(double x, double* sn, double* cs) {
   const double shift = 6755399441055744.0;  // 1.5 * 2^52
-  const double t = fma(x, 2.0, shift);
-  const int q = __double2loint(t) & 3;
+  const double t = fma(x, 4.0, shift);
+  const int q = __double2loint(t);
   const double k = t - shift;
-  const double r = fma(k, -0.5, x);
-  const double r2 = r * r;
-  double ps = 0x1.aaec32af93359p-21;
-  ps = fma(ps, r2, -0x1.6fadb9f155744p-16);
-  ps = fma(ps, r2, 0x1.e8f434d018d63p-12);
-  ps = fma(ps, r2, -0x1.e3074fde8871fp-8);
-  ps = fma(ps, r2, 0x1.50783487ee782p-4);
-  ps = fma(ps, r2, -0x1.32d2cce62bd86p-1);
-  ps = fma(ps, r2, 0x1.466bc6775aae2p+1);
-  ps = fma(ps, r2, -0x1.4abbce625be53p+2);
-  ps = fma(ps, r2, 0x1.921fb54442d18p+1);
-  const double s = r * ps;
-  double pc = 0x1.20c62c2f2d7f5p-18;
-  pc = fma(pc, r2, -0x1.b6e24f44b128fp-14);
-  pc = fma(pc, r2, 0x1.f9d38a3763cc3p-10);
-  pc = fma(pc, r2, -0x1.a6d1f2a204a8cp-6);
-  pc = fma(pc, r2, 0x1.e1f506891babbp-3);
-  pc = fma(pc, r2, -0x1.55d3c7e3cbffap+0);
-  pc = fma(pc, r2, 0x1.03c1f081b5ac4p+2);
-  pc = fma(pc, r2, -0x1.3bd3cc9be45dep+2);
-  const double c = fma(pc, r2, 1.0);
-  // rotate by q quarter turns
+  const double r = fma(k, -0.25, x);
+  const double u = r * r;
+  double p = 0x1.e3eed5d16d705p+1;
+  p = fma(p, u, -0x1.e30063a031f57p+3);
+  p = fma(p, u, 0x1.50782fca38c0ep+5);
+  p = fma(p, u, -0x1.32d2cce2d5361p+6);
+  p = fma(p, u, 0x1.466bc67758700p+6);
+  p = fma(p, u, -0x1.4abbce625be41p+5);
+  p = fma(p, u, 0x1.921fb54442d18p+2);
+  const double s = r * p;
+  double c = -0x1.b26fe85b71b00p+0;
+  c = fma(c, u, 0x1.f9cc6acfc67d7p+2);
+  c = fma(c, u, -0x1.a6d1ecb740183p+4);
+  c = fma(c, u, 0x1.e1f50683b42cap+5);
+  c = fma(c, u, -0x1.55d3c7e3c95bcp+6);
+  c = fma(c, u, 0x1.03c1f081b5ab0p+6);
+  c = fma(c, u, -0x1.3bd3cc9be45dep+4);
+  c = fma(c, u, 1.0);
+  // quarter turns: (sin, cos) of q pi/2 + a = (s, c), (c, -s), (-s, -c), (-c, s)
   const double a = (q & 1) ? c : s;
   const double b = (q & 1) ? s : c;
-  *sn = (q & 2) ? -a : a;
-  *cs = ((q + 1) & 2) ? -b : b;
+  const unsigned fa = (unsigned)(q & 2) << 30, fb = (unsigned)((q + 1) & 2) << 30;
+  *sn = __hiloint2double((int)((unsigned)__double2hiint(a) ^ fa), __double2loint(a));
+  *cs = __hiloint2double((int)((unsigned)__double2hiint(b) ^ fb), __double2loint(b));
 }
+
+// Right-hand sides used by the adaptive kernels expose their time-only part
+// separately: drive(t) evaluates it, fd(d, t, y, dy) the rest.  A Cash-Karp
+// trial ends at t + h, where the next trial's first stage starts, so the
+// kernels carry that stage's drive over instead of evaluating it twice.
+// Autonomous systems use NoDrive.
+struct NoDrive {};
 
 // ---------------------------------------------------------------------------
 // Dimensionless Keller-Miksis (Sec. 4.2, Eqs. dimensionless_system1-2,
@@ -130,22 +168,25 @@ __device__ __forceinline__ void sincospi_poly(double x, double* sn, double* cs) 
 //          - (C5 sin 2 pi tau + C6 sin(2 pi C11 tau + C12)) (1 + C9 y2)
 //          - y1 (C7 cos 2 pi tau + C8 cos(2 pi C11 tau + C12)),
 //   D_KM = y1 - C9 y1 y2 + C4 C9.
-// Following the paper's cost notes (Sec. 3.3): one division yields both
+// Following the paper's cost notes (Sec. 3.3): one reciprocal yields both
 // 1/y1 (shared by the three 1/y1 terms) and 1/D_KM, sine and cosine of one
-// angle come from one evaluation (sincospi_poly, with the angle 2 pi tau
-// passed as 2 tau in units of pi), and the rational power is not sent
-// through pow(): with EXP215 the exponent
-// C10 = 3 gamma = 4.2 = 21/5 (gamma = 1.4) is applied as
+// angle come from one evaluation (sincos2pi_poly), and the rational power is
+// not sent through pow(): with EXP215 the exponent C10 = 3 gamma = 4.2 = 21/5
+// (gamma = 1.4) is applied as
 //   (1/y1)^(21/5) = (1/y1)^4 * y1^(-1/5)
 // with y1^(-1/5) from inv_fifth_root (the host selects this form when every
 // system's C10 lies within 4 ulp of 21/5; otherwise pow() is used).
+// The two forcing sums depend on tau alone and form the Drive.
 // DUAL selects the second driving frequency (C6, C8 != 0).
 // ---------------------------------------------------------------------------
 template <bool DUAL, bool EXP215 = false>
 struct KellerMiksis {
   static constexpr int kDim = 2;
   static constexpr int kPar = 13;
-  double C0, C1, C2, C3, C4, C5, C6, C7, C8, C9, C10, C11, C12pi, C4C9;
+  double C0, C1, C2, C3, C4, C5, C6, C7, C8, C9, C10, C11, C12f, C4C9;
+  struct Drive {
+    double fs, fc;  // C5 sin 2 pi tau + C6 sin(...), C7 cos 2 pi tau + C8 cos(...)
+  };
   __device__ __forceinline__ void load(const double* P, int64_t n, int64_t i) {
     C0 = P[i];
     C1 = P[n + i];
@@ -159,14 +200,27 @@ struct KellerMiksis {
     C9 = P[9 * n + i];
     C10 = P[10 * n + i];
     C11 = P[11 * n + i];
-    C12pi = P[12 * n + i] * (1.0 / 3.141592653589793238462643383279502884);
+    C12f = P[12 * n + i] * (0.5 / 3.141592653589793238462643383279502884);  // C12 in turns
     C4C9 = C4 * C9;
   }
-  __device__ __forceinline__ void f(double tau, const double* y, double* dy) const {
+  __device__ __forceinline__ Drive drive(double tau) const {
+    double s1, c1;
+    sincos2pi_poly(tau, &s1, &c1);
+    Drive d{C5 * s1, C7 * c1};
+    if (DUAL) {
+      double s2, c2;
+      sincos2pi_poly(fma(C11, tau, C12f), &s2, &c2);
+      d.fs = fma(C6, s2, d.fs);
+      d.fc = fma(C8, c2, d.fc);
+    }
+    return d;
+  }
+  __device__ __forceinline__ void fd(const Drive& d, double tau, const double* y, double* dy) const {
+    (void)tau;
     const double y1 = y[0], y2 = y[1];
-    // one division serves both 1/y1 and 1/D: w = 1 / (y1 D), 1/y1 = D w, N/D = N y1 w
+    // one reciprocal serves both 1/y1 and 1/D: w = 1 / (y1 D), 1/y1 = D w, N/D = N y1 w
     const double D = fma(-C9 * y1, y2, y1) + C4C9;
-    const double w = 1.0 / (y1 * D);
+    const double w = rcp_nr(y1 * D);
     const double rx = D * w;
     double g;
     if (EXP215) {
@@ -175,27 +229,20 @@ struct KellerMiksis {
     } else {
       g = pow(rx, C10);
     }
-    double s1, c1;
-    sincospi_poly(2.0 * tau, &s1, &c1);
     const double one_c9y2 = fma(C9, y2, 1.0);
-    double forc_s = C5 * s1;
-    double forc_c = C7 * c1;
-    if (DUAL) {
-      double s2, c2;
-      sincospi_poly(fma(2.0 * C11, tau, C12pi), &s2, &c2);
-      forc_s = fma(C6, s2, forc_s);
-      forc_c = fma(C8, c2, forc_c);
-    }
     // (1 - C9 y2 / 3) * 1.5 * y2^2 = (1.5 - 0.5 C9 y2) y2^2
     const double kin = fma(-0.5 * C9, y2, 1.5) * (y2 * y2);
     double N = fma(C1, y2, C0) * g;
     N = fma(-C2, one_c9y2, N);
     N = fma(-fma(C4, y2, C3), rx, N);
     N -= kin;
-    N = fma(-forc_s, one_c9y2, N);
-    N = fma(-y1, forc_c, N);
+    N = fma(-d.fs, one_c9y2, N);
+    N = fma(-y1, d.fc, N);
     dy[0] = y2;
     dy[1] = N * (y1 * w);
+  }
+  __device__ __forceinline__ void f(double tau, const double* y, double* dy) const {
+    fd(drive(tau), tau, y, dy);
   }
 };
 
@@ -222,6 +269,9 @@ struct ReliefValve {
     dy[1] = fma(-kappa, y[1], y[2] - (y[0] + delta));
     dy[2] = beta * fma(-y[0], sqrt(fmax(y[2], 0.0)), q);
   }
+  using Drive = NoDrive;
+  __device__ __forceinline__ Drive drive(double) const { return {}; }
+  __device__ __forceinline__ void fd(const Drive&, double t, const double* y, double* dy) const { f(t, y, dy); }
 };
 
 }  // namespace ens

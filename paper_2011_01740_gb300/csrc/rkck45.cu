@@ -30,35 +30,45 @@
 namespace ens {
 
 // ---------------------------------------------------------------------------
-// one Cash-Karp trial: stages 2..6 from k1, fifth-order solution and error
+// one Cash-Karp trial: stages 2..6 from k1, fifth-order solution and error.
+// d5 receives the drive (time-only part of the RHS) at t + h, the time of
+// the next trial's first stage after an accepted step.
 // ---------------------------------------------------------------------------
 template <class Sys>
 __device__ __forceinline__ void ck_trial(const Sys& s, double t, double h, const double* y,
-                                         const double* k1, double* y5, double* err) {
+                                         const double* k1, double* y5, double* err,
+                                         typename Sys::Drive& d5) {
   constexpr int D = Sys::kDim;
   double k2[D], k3[D], k4[D], k5[D], k6[D], ys[D];
+  double ts;
 #pragma unroll
   for (int c = 0; c < D; ++c) ys[c] = fma(h, ck::a21 * k1[c], y[c]);
-  s.f(fma(ck::c2, h, t), ys, k2);
+  ts = fma(ck::c2, h, t);
+  s.fd(s.drive(ts), ts, ys, k2);
 #pragma unroll
   for (int c = 0; c < D; ++c) ys[c] = fma(h, fma(ck::a32, k2[c], ck::a31 * k1[c]), y[c]);
-  s.f(fma(ck::c3, h, t), ys, k3);
+  ts = fma(ck::c3, h, t);
+  s.fd(s.drive(ts), ts, ys, k3);
 #pragma unroll
   for (int c = 0; c < D; ++c)
     ys[c] = fma(h, fma(ck::a43, k3[c], fma(ck::a42, k2[c], ck::a41 * k1[c])), y[c]);
-  s.f(fma(ck::c4, h, t), ys, k4);
+  ts = fma(ck::c4, h, t);
+  s.fd(s.drive(ts), ts, ys, k4);
 #pragma unroll
   for (int c = 0; c < D; ++c)
     ys[c] = fma(h, fma(ck::a54, k4[c], fma(ck::a53, k3[c], fma(ck::a52, k2[c], ck::a51 * k1[c]))),
                 y[c]);
-  s.f(t + h, ys, k5);  // c5 = 1
+  ts = t + h;  // c5 = 1
+  d5 = s.drive(ts);
+  s.fd(d5, ts, ys, k5);
 #pragma unroll
   for (int c = 0; c < D; ++c)
     ys[c] = fma(h,
                 fma(ck::a65, k5[c],
                     fma(ck::a64, k4[c], fma(ck::a63, k3[c], fma(ck::a62, k2[c], ck::a61 * k1[c])))),
                 y[c]);
-  s.f(fma(ck::c6, h, t), ys, k6);
+  ts = fma(ck::c6, h, t);
+  s.fd(s.drive(ts), ts, ys, k6);
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     y5[c] = fma(h, fma(ck::b6, k6[c], fma(ck::b4, k4[c], fma(ck::b3, k3[c], ck::b1 * k1[c]))), y[c]);
@@ -119,6 +129,8 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
   int64_t i = claim(a, true);
   bool timed_out = false;
   Sys s;
+  // drive at the phase start (tau = t0), at the current tau, and at tau + h
+  typename Sys::Drive d0, dk, d5;
   double y[D], k1[D], y5[D], err[D];
   double tau = a.t0, dt = a.dt0, ymax = 0.0, ymin = 0.0;
   int32_t ph = 0, st = 0;
@@ -136,6 +148,8 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
     trials = nacc = nrej = nrhs = 0;
     k1v = false;
     ymax = ymin = y[0];
+    d0 = s.drive(a.t0);
+    dk = d0;
   };
   auto finish_system = [&](int64_t sys) {
     // phases that were not completed are marked NaN
@@ -181,17 +195,18 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
         clamped = true;
       }
       if (!k1v) {
-        s.f(tau, y, k1);
+        s.fd(dk, tau, y, k1);
         ++nrhs;
         k1v = true;
       }
-      ck_trial(s, tau, h, y, k1, y5, err);
+      ck_trial(s, tau, h, y, k1, y5, err, d5);
       nrhs += 5;
       ++trials;
       const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
       const double fac = step_factor(E);
       if (E <= 1.0) {
         tau = clamped ? tau_end : tau + h;
+        dk = d5;  // tau + h, the time of stage 5; a phase end below resets it
 #pragma unroll
         for (int c = 0; c < D; ++c) y[c] = y5[c];
         k1v = false;
@@ -211,6 +226,7 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
             sys_done = true;
           } else {
             tau = a.t0;
+            dk = d0;
             ymax = ymin = y[0];
           }
         }
@@ -234,9 +250,9 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
 // of y1, the Poincare section), both falling, absolute tolerance event_tol:
 //   - after a trial that passes the error test, the impact overshoots when
 //     y1(t+h) < -tol, the maximum when y2(t) > tol and y2(t+h) < -tol; the
-//     trial is redone with the step cut by the secant fraction g(t) /
-//     (g(t) - g(t+h)) of the earliest overshooting event (one half when the
-//     impact starts inside the band |y1| <= tol);
+//     trial is redone with the step cut to the earliest overshooting event's
+//     estimated root, event_frac (one half when the impact starts inside the
+//     band |y1| <= tol);
 //   - otherwise the step is accepted; at its end the maximum is located when
 //     y2(t) > tol and |y2| <= tol (y1 goes to the ring of Poincare points), the
 //     impact when |y1| <= tol and y2 < 0 (y1 <- 0, y2 <- -r y2, Eqs.
@@ -246,6 +262,25 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
 //     the seat: y1 = y2 = 0 while y3 rises as beta q until y3 = delta, an
 //     interval advanced in closed form.
 // ---------------------------------------------------------------------------
+// Root estimate of a falling event function over a trial of length h, as a
+// fraction of h: g0 > 0 with slope d0 at the start (from k1), g1 < 0 at the
+// end.  The quadratic g0 + B x + A x^2 (B = d0 h, A = g1 - g0 - B) changes
+// sign once on (0, 1), at x = 2 g0 / (-B + sqrt(B^2 - 4 A g0)) for either sign
+// of A.  It is exact for a constant second derivative, so retries converge at
+// grazing impacts, where a chord from the fixed start of the retried step
+// closes in only linearly.  The chord g0 / (g0 - g1) stands in if rounding
+// takes the root out of (0, 1).
+__device__ __forceinline__ double event_frac(double g0, double d0, double g1, double h) {
+  const double B = d0 * h;
+  const double A = g1 - g0 - B;
+  const double D = fma(B, B, -4.0 * A * g0);
+  const double chord = g0 / (g0 - g1);
+  if (!(D >= 0.0)) return chord;
+  const double den = sqrt(D) - B;
+  const double x = 2.0 * g0 / den;
+  return (den > 0.0 && x > 0.0 && x < 1.0) ? x : chord;
+}
+
 __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
   using Sys = ReliefValve;
   constexpr int D = Sys::kDim;
@@ -254,6 +289,7 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
   int64_t i = claim(a, true);
   bool timed_out = false;
   Sys s;
+  Sys::Drive d5;  // autonomous: empty
   double y[D], k1[D], y5[D], err[D];
   double t = a.t0, dt = a.dt0, h_ev = 0.0, ymin = 0.0;
   int32_t st = 0, ev_retries = 0;
@@ -331,7 +367,7 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
         ++nrhs;
         k1v = true;
       }
-      ck_trial(s, t, h, y, k1, y5, err);
+      ck_trial(s, t, h, y, k1, y5, err, d5);
       nrhs += 5;
       ++trials;
       const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
@@ -345,12 +381,12 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
         double best = 2.0;
         bool overshoot = false;
         if (y5[0] < -etol) {  // impact beyond the band
-          const double frac = (y[0] > etol) ? y[0] / (y[0] - y5[0]) : 0.5;
+          const double frac = (y[0] > etol) ? event_frac(y[0], k1[0], y5[0], h) : 0.5;
           best = frac < best ? frac : best;
           overshoot = true;
         }
         if (y[1] > etol && y5[1] < -etol) {  // maximum beyond the band
-          const double frac = y[1] / (y[1] - y5[1]);
+          const double frac = event_frac(y[1], k1[1], y5[1], h);
           best = frac < best ? frac : best;
           overshoot = true;
         }
@@ -408,6 +444,7 @@ __global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
   int64_t i = claim(a, true);
   bool timed_out = false;
   Sys s;
+  typename Sys::Drive dk, d5;  // drive at t and at t + h
   double y[D], k1[D], y5[D], err[D];
   double t = a.t0, dt = a.dt0;
   int32_t st = 0;
@@ -422,6 +459,7 @@ __global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
     st = timed_out ? kStTimeout : 0;
     trials = nacc = nrej = nrhs = 0;
     k1v = false;
+    dk = s.drive(a.t0);
   };
   auto finish_system = [&](int64_t sys) {
 #pragma unroll
@@ -452,17 +490,18 @@ __global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
         clamped = true;
       }
       if (!k1v) {
-        s.f(t, y, k1);
+        s.fd(dk, t, y, k1);
         ++nrhs;
         k1v = true;
       }
-      ck_trial(s, t, h, y, k1, y5, err);
+      ck_trial(s, t, h, y, k1, y5, err, d5);
       nrhs += 5;
       ++trials;
       const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
       const double fac = step_factor(E);
       if (E <= 1.0) {
         t = clamped ? a.t1 : t + h;
+        dk = d5;  // t + h; a clamped step ends the system
 #pragma unroll
         for (int c = 0; c < D; ++c) y[c] = y5[c];
         k1v = false;
@@ -490,8 +529,13 @@ __global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
 // Adapter so that fixed-step systems can run through the adaptive kernels.
 template <class Fixed>
 struct AdaptFixed : Fixed {
+  using Drive = NoDrive;
   __device__ __forceinline__ void f(double t, const double* y, double* dy) const {
     Fixed::template f<false>(t, y, dy);
+  }
+  __device__ __forceinline__ Drive drive(double) const { return {}; }
+  __device__ __forceinline__ void fd(const Drive&, double t, const double* y, double* dy) const {
+    f(t, y, dy);
   }
 };
 

@@ -232,6 +232,22 @@ def test_prv_full_sweep_sampled_parity():
     assert np.all(g["y"][2] >= 0.0)
 
 
+def test_prv_grazing_impact_matches_oracle():
+    """A recorded valve state (q = 7.5393) that dips about 1e-5 below the seat
+    under a strong opening force: the event location must converge on the
+    GPU (no EVENT_NO_CONVERGE), with one impact and the oracle's end state,
+    from three initial step proposals."""
+    params = np.array([[7.5392987796736906], [1.25], [10.0], [20.0], [0.8]])
+    y0 = np.array([[0.0013698420381308958], [-0.3162497537150412], [45.746744783524875]])
+    for dt0 in (0.0085, 0.008889370476683223, 0.0107):
+        kw = dict(rtol=1e-10, atol=1e-10, dt0=dt0, dt_min=1e-14, dt_max=1.0, event_tol=1e-6, acc_t_start=0.0)
+        g = solve_gpu(ens.ENS_SYS_RELIEF_VALVE, params, y0, (0.0, 0.05), ens.ENS_RKCK45, ens.make_tol(**kw))
+        r = oracle.cashkarp_solve(oracle.PRV, params, y0, oracle.make_tol(t0=0.0, t1=0.05, **kw))
+        assert g["status"][0] == 0 and r["status"][0] == 0
+        assert g["acc"][34, 0] == 1 and r["acc"][34, 0] == 1
+        assert np.all(rel_err(g["y"], r["y"]) < 1e-7), (g["y"][:, 0], r["y"][:, 0])
+
+
 def test_prv_launch_modes_bitwise_identical():
     wl = _prv(200, 32.0)
     ref = _prv_gpu(wl, launch=ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=128))
@@ -239,6 +255,33 @@ def test_prv_launch_modes_bitwise_identical():
                                             cost_order=1))
     for k in ("y", "acc", "nacc", "nrej", "status"):
         assert np.array_equal(g[k], ref[k], equal_nan=True), k
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_kernel_ms_times_the_main_launch(use_graph):
+    """ens_kernel_ms: positive, and below the whole solve (which adds the
+    one-phase pilot and the claim-order sort), with and without graph replay."""
+    import torch
+    km = W.km(24, 24, n_phases=4)
+    C = km_coeffs_lib(km["phys"], km["liquid"])
+    ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
+                         ens.ENS_RKCK45, ens_tol_from(km["tol"]))
+    try:
+        with pytest.raises(ens.EnsError):
+            ens.ens_kernel_ms(ctx)                      # nothing enqueued yet
+        ens.ens_set_launch(ctx, ens.make_launch(block=160, blocks_per_sm=1, use_graph=use_graph, cost_order=1))
+        s = torch.cuda.Stream()
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            ens.ens_solve(ctx, s)
+            e1.record(s)
+            assert ens.ens_sync(ctx) == ens.ENS_OK
+            s.synchronize()
+            k = ens.ens_kernel_ms(ctx)
+            assert 0.0 < k <= e0.elapsed_time(e1) * 1.001, (k, e0.elapsed_time(e1))
+    finally:
+        ens.ens_destroy(ctx)
 
 
 def test_autotune_returns_a_valid_launch():

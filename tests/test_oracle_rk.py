@@ -224,3 +224,11 @@ def test_rhs_evaluation_count_reuses_k1_after_rejection():
     n_trials = r["nacc"][0] + r["nrej"][0]
     # 6 evaluations per trial, minus the first stage of every retried trial
     assert r["nrhs"][0] == 6 * n_trials - r["nrej"][0]
+
+
+def test_single_thread_call_leaves_the_thread_default_alone():
+    """nthreads applies to one call only (the timed baselines rely on it)."""
+    before = oracle.max_threads()
+    y0 = np.array([[1.0, 2.0]])
+    oracle.rk4_solve(oracle.LINEAR, np.array([[-1.0, -2.0]]), y0, 0.0, 0.01, 10, nthreads=1)
+    assert oracle.max_threads() == before

@@ -297,6 +297,43 @@ def test_bouncing_ball_event_location_and_impact_law():
     assert r["acc"][32, 0] == 0.0           # it touched the floor
 
 
+def test_grazing_impact_is_located_at_the_closed_form_root():
+    """Ball with upward acceleration (g < 0) approaching the floor: y1 = h0 +
+    v0 t - g t^2 / 2 dips 1.2e-5 below the seat, far less than the step, a
+    grazing impact.  The first crossing is t* = (-v0 - sqrt(v0^2 - 2 |g| h0))
+    / |g|; after the impact law y2 <- -r y2 the flight is again a parabola, so
+    y1(T) has a closed form.  Cash-Karp integrates the quadratic exactly, so
+    only the event location separates the solver from it."""
+    g, rr, h0, v0 = -36.14, 0.8, 0.00137, -0.316
+    a = -g
+    ts = (-v0 - math.sqrt(v0 * v0 - 2.0 * a * h0)) / a
+    vs = v0 + a * ts
+    T = 0.02
+    vp = -rr * vs
+    y_T = vp * (T - ts) + 0.5 * a * (T - ts) ** 2
+    tol = oracle.make_tol(rtol=1e-10, atol=1e-10, dt0=0.0089, dt_min=1e-14, dt_max=1.0,
+                          event_tol=1e-6, t0=0.0, t1=T, acc_t_start=0.0)
+    r = oracle.cashkarp_solve(oracle.BALL, [[g], [rr]], [[h0], [v0], [0.0]], tol)
+    assert r["status"][0] == 0
+    assert int(r["acc"][34, 0]) == 1
+    assert abs(r["y"][0, 0] - y_T) < 1e-9, (r["y"][0, 0], y_T)
+    assert r["nrej"][0] + r["nacc"][0] < 40
+
+
+def test_prv_grazing_impact_from_a_recorded_state():
+    """A valve state near the edge of the impacting range (q = 7.5393) that
+    approaches the seat at y2 = -0.316 under a strong opening force and dips
+    about 1e-5 below it: the impact must be located (status 0, one impact)."""
+    q = 7.5392987796736906
+    y0 = np.array([[0.0013698420381308958], [-0.3162497537150412], [45.746744783524875]])
+    tol = oracle.make_tol(rtol=1e-10, atol=1e-10, dt0=0.008889370476683223, dt_min=1e-14, dt_max=1.0,
+                          event_tol=1e-6, t0=0.0, t1=0.05, acc_t_start=0.0)
+    r = oracle.cashkarp_solve(oracle.PRV, _prv_params(q), y0, tol)
+    assert r["status"][0] == 0
+    assert int(r["acc"][34, 0]) == 1
+    assert r["acc"][32, 0] == 0.0
+
+
 def test_prv_impacts_keep_body_on_or_above_seat():
     q = np.array([0.5, 2.0, 6.0])
     y0 = np.stack([np.full(3, 0.2), np.zeros(3), np.zeros(3)])
