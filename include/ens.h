@@ -291,6 +291,10 @@ typedef struct {
     int32_t batch;         /* samples per Adam step                             */
     float lr, beta1, beta2, eps;   /* Adam (Kingma & Ba 2015)                    */
     uint64_t seed;         /* shuffle stream (splitmix64)                        */
+    float lr_final;        /* > 0: cosine decay of the Adam step size from lr
+                              (first step) to lr_final (last step) over all
+                              epochs (Loshchilov & Hutter 2017, no restarts);
+                              0: constant lr                                     */
 } ens_train_cfg;
 
 /* Create `members` (1..8) networks; weights uniform in +-1/sqrt(fan_in),

@@ -353,11 +353,12 @@ def ens_km_coefficients(pA1, f1, pA2, f2, theta, RE, liquid: dict, out=None, str
 class EnsTrainCfg(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("lr_final", ctypes.c_float)]
 
 
-def make_train_cfg(epochs=50, batch=1024, lr=2e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=20201103):
-    return EnsTrainCfg(int(epochs), int(batch), lr, beta1, beta2, eps, int(seed))
+def make_train_cfg(epochs=50, batch=1024, lr=2e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=20201103,
+                   lr_final=0.0):
+    return EnsTrainCfg(int(epochs), int(batch), lr, beta1, beta2, eps, int(seed), lr_final)
 
 
 _mlp_bound = False

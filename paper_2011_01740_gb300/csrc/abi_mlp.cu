@@ -365,7 +365,8 @@ ens_status ens_mlp_loss_grad(ens_mlp* m, int64_t n, const float* x, const float*
 
 ens_status ens_mlp_train(ens_mlp* m, int64_t n, const float* x, const float* y, const ens_train_cfg* cfg,
                          float* loss_hist, void* stream) {
-  if (!m || n <= 0 || !cfg || cfg->epochs < 0 || cfg->batch <= 0 || !(cfg->lr > 0.f)) return ENS_EINVAL;
+  if (!m || n <= 0 || !cfg || cfg->epochs < 0 || cfg->batch <= 0 || !(cfg->lr > 0.f) || !(cfg->lr_final >= 0.f))
+    return ENS_EINVAL;
   if (n > 0x7fffffffLL) return ENS_EINVAL;
   if (!is_device(x) || !is_device(y)) {
     merr(m, "ens_mlp_train: x and y must be device memory");
@@ -387,6 +388,8 @@ ens_status ens_mlp_train(ens_mlp* m, int64_t n, const float* x, const float* y, 
   e = cudaMemsetAsync(hist_d, 0, (size_t)std::max(1, cfg->epochs) * m->members * sizeof(float), s);
   std::vector<int32_t> perm(n);
   const int64_t tot = (int64_t)m->members * mlp::kP;
+  const int64_t steps_total = (int64_t)cfg->epochs * ((n + B - 1) / B);
+  int64_t step = 0;
   for (int ep = 0; ep < cfg->epochs && e == cudaSuccess; ++ep) {
     // Fisher-Yates with splitmix64 draws (stream seed + epoch)
     for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
@@ -406,7 +409,14 @@ ens_status ens_mlp_train(ens_mlp* m, int64_t n, const float* x, const float* y, 
       m->adam_t += 1;
       const float c1 = 1.0f - powf(cfg->beta1, (float)m->adam_t);
       const float c2 = 1.0f - powf(cfg->beta2, (float)m->adam_t);
-      e = mlp::launch_adam(tot, m->master, m->wbf, m->grad, m->m1, m->m2, cfg->lr, cfg->beta1, cfg->beta2,
+      // cosine schedule: lr at the first step, lr_final at the last
+      float lr = cfg->lr;
+      if (cfg->lr_final > 0.f && steps_total > 1) {
+        const double x = (double)step / (double)(steps_total - 1);
+        lr = (float)(cfg->lr_final + 0.5 * (cfg->lr - cfg->lr_final) * (1.0 + cos(3.14159265358979323846 * x)));
+      }
+      ++step;
+      e = mlp::launch_adam(tot, m->master, m->wbf, m->grad, m->m1, m->m2, lr, cfg->beta1, cfg->beta2,
                            cfg->eps, c1, c2, s);
     }
     if (st != ENS_OK) break;

@@ -77,7 +77,7 @@ def training_set_from_acc(ens, km: dict, acc, n_phases: int, first_phase: int, d
 
 
 def run(ens, train_shape=(362, 362), screen_m=1024, n_phases=64, first_phase=32, threshold=0.05,
-        members=4, epochs=150, batch=1024, lr=2e-3, seed=W.SEED, stream=None, validate=2048,
+        members=4, epochs=150, batch=1024, lr=2e-3, lr_final=2e-5, seed=W.SEED, stream=None, validate=2048,
         liquid=None, train=None):
     """Train on a train_shape grid, screen a screen_m x screen_m log grid,
     re-solve the uncertain points; returns timings, counts and errors.
@@ -108,7 +108,8 @@ def run(ens, train_shape=(362, 362), screen_m=1024, n_phases=64, first_phase=32,
     try:
         t0 = time.perf_counter()
         hist = ens.ens_mlp_train(m, x_tr.shape[0], x_tr, y_tr,
-                                 ens.make_train_cfg(epochs=epochs, batch=batch, lr=lr, seed=seed), members,
+                                 ens.make_train_cfg(epochs=epochs, batch=batch, lr=lr, seed=seed,
+                                                    lr_final=lr_final), members,
                                  stream=stream)
         out["train_s"] = time.perf_counter() - t0
         out["train_loss_first_last"] = [float(hist[0].mean()), float(hist[-1].mean())]
