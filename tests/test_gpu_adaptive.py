@@ -102,6 +102,21 @@ def test_km_launch_modes_and_graph_replay_are_bitwise_identical():
             assert np.array_equal(g[k], ref[k], equal_nan=True), (k, L.as_dict())
 
 
+def test_persistent_refill_solves_every_system_as_the_plain_launch():
+    """30,000 systems on 4,864 to 34,048 persistent lanes: lanes refill from
+    the claim counter many times over (longest-first or in index order), and
+    every system comes out bitwise as in the plain one-thread-per-system launch."""
+    km = W.km(150, 200, n_phases=2)
+    ref = _km_gpu(km, launch=ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=128))
+    for L in (ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=160, blocks_per_sm=1, cost_order=1),
+              ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=224, blocks_per_sm=1, cost_order=0),
+              ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=32, blocks_per_sm=1, cost_order=1)):
+        g = _km_gpu(km, launch=L)
+        assert np.all(g["nacc"] > 0)
+        for k in ("y", "acc", "nacc", "nrej", "nrhs", "status", "dt"):
+            assert np.array_equal(g[k], ref[k], equal_nan=True), (k, L.as_dict())
+
+
 def test_km_graph_replays_and_set_inputs():
     km = W.km(9, 11, n_phases=2)
     C = km_coeffs_lib(km["phys"], km["liquid"])
