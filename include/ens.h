@@ -120,6 +120,9 @@ enum {
  *                  integrations over tau in [t_span[0], t_span[0] + phase_len],
  *                  tau reset at each phase start; accessories per phase.
  *   acc_t_start    relief valve: the y1 minimum accessory covers t >= it.
+ *   n_transient    phase mode: the first n_transient phases are integrated but
+ *                  not recorded (the paper's transient phases, Sec. 4.2);
+ *                  0 <= n_transient < n_phases (0 outside phase mode).
  *   prec           ens_precision.
  *   timeout_s      wall-clock budget of one ens_solve on the device; systems
  *                  still running are stopped with ENS_SYS_TIMEOUT (<= 0: 600 s). */
@@ -134,6 +137,7 @@ typedef struct {
     double phase_len;
     double acc_t_start;
     double timeout_s;
+    int32_t n_transient;
 } ens_tol;
 
 /* Launch configuration (see ens_set_launch / ens_autotune).
@@ -217,9 +221,9 @@ ens_status ens_kernel_ms(ens_ctx *ctx, double *ms);
 ens_status ens_read(ens_ctx *ctx, int which, void *dst, size_t dst_bytes);
 
 /* Number of accessory rows of ENS_ACC for this context:
- *   phase mode (Keller-Miksis): 2 * n_phases, row 2k = max y1 in phase k,
- *     row 2k+1 = min y1 in phase k, taken over the natural step points and the
- *     phase start (no dense output, Sec. 4.2.1);
+ *   phase mode (Keller-Miksis): 2 * (n_phases - n_transient), row 2k = max y1
+ *     in phase n_transient + k, row 2k+1 = its min y1, taken over the natural
+ *     step points and the phase start (no dense output, Sec. 4.2.1);
  *   relief valve: 35 rows: rows 0..31 ring of the last Poincare maxima of y1
  *     (slot m mod 32 holds maximum number m; NaN if unused), row 32 the
  *     minimum of y1 for t >= acc_t_start, row 33 the number of maxima, row 34
@@ -370,7 +374,8 @@ ens_status ens_eval_rhs(ens_system sys, int64_t n, const double *params, const d
  *   params [npar][n], y0 [dim][n]                       inputs (not modified)
  *   y [dim][n], t_out [n], dt_out [n], acc [rows][n],
  *   status [n] (int32), nacc, nrej, nrhs [n] (int64)    outputs
- * (rows as ens_acc_rows would give: 2 n_phases, or 35 for the relief valve).
+ * (rows as ens_acc_rows would give: 2 (n_phases - n_transient), or 35 for
+ * the relief valve).
  * cost_order != 0 claims systems longest first after a one-phase pilot
  * (written into the output buffers, then overwritten).
  *

@@ -31,6 +31,7 @@ _lib = None
 
 # system identifiers (mirror the enum in oracle.c)
 X2P, LORENZ, KM, PRV, LINEAR, TPOW, BALL = range(7)
+CASHKARP, DOPRI5 = 0, 1                     # Tol.method
 DIM = {X2P: 1, LORENZ: 3, KM: 2, PRV: 3, LINEAR: 1, TPOW: 1, BALL: 3}
 NPAR = {X2P: 1, LORENZ: 3, KM: 13, PRV: 5, LINEAR: 1, TPOW: 2, BALL: 2}
 
@@ -50,7 +51,7 @@ class Tol(ctypes.Structure):
                 ("event_tol", ctypes.c_double), ("max_steps", ctypes.c_int64),
                 ("n_phases", ctypes.c_int32), ("phase_len", ctypes.c_double),
                 ("t0", ctypes.c_double), ("t1", ctypes.c_double),
-                ("acc_t_start", ctypes.c_double)]
+                ("acc_t_start", ctypes.c_double), ("method", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -84,6 +85,8 @@ def lib():
         L.orc_rk4_solve.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int64, i32p, ctypes.c_int]
         L.orc_cashkarp_tableau.argtypes = [dp, dp, dp, dp]
+        L.orc_dopri5_tableau.argtypes = [dp, dp, dp, dp]
+        L.orc_dopri5_step.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
         L.orc_cashkarp_step.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp,
                                         dp, dp]
         L.orc_cashkarp_solve.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp,
@@ -181,6 +184,24 @@ def cashkarp_tableau():
     return c, a.reshape(6, 6), b, bs
 
 
+def dopri5_tableau():
+    c = np.empty(7)
+    a = np.empty(49)
+    b = np.empty(7)
+    bs = np.empty(7)
+    lib().orc_dopri5_tableau(_d(c), _d(a), _d(b), _d(bs))
+    return c, a.reshape(7, 7), b, bs
+
+
+def dopri5_step(sys: int, p, t: float, h: float, y):
+    p = _c64(p)
+    y = _c64(y)
+    y5 = np.empty(DIM[sys])
+    err = np.empty(DIM[sys])
+    lib().orc_dopri5_step(sys, _d(p), t, h, _d(y), _d(y5), _d(err))
+    return y5, err
+
+
 def cashkarp_step(sys: int, p, t: float, h: float, y):
     p = _c64(p)
     y = _c64(y)
@@ -192,9 +213,10 @@ def cashkarp_step(sys: int, p, t: float, h: float, y):
 
 def make_tol(rtol=1e-10, atol=1e-10, dt0=1e-2, dt_min=1e-14, dt_max=1e-1, event_tol=1e-6,
              max_steps=10**9, n_phases=0, phase_len=1.0, t0=0.0, t1=1.0,
-             acc_t_start=0.0) -> Tol:
+             acc_t_start=0.0, method=0) -> Tol:
+    """method: CASHKARP (0) or DOPRI5 (1)."""
     return Tol(rtol, atol, dt0, dt_min, dt_max, event_tol, int(max_steps), int(n_phases),
-               phase_len, t0, t1, acc_t_start)
+               phase_len, t0, t1, acc_t_start, int(method))
 
 
 def n_acc_rows(sys: int, tol: Tol) -> int:

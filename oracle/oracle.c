@@ -401,6 +401,76 @@ void orc_cashkarp_step(int sys, const double *p, double t, double h, const doubl
 }
 
 /* ------------------------------------------------------------------------- */
+/* Dormand-Prince embedded Runge-Kutta 5(4), "DOPRI5"                        */
+/* ------------------------------------------------------------------------- */
+
+/* Dormand & Prince (1980): seven stages, the seventh at c7 = 1 with coupling
+ * row a7j = b_j, so that k7 = f(t + h, y5) ("first same as last": after an
+ * accepted step k7 is the next step's k1).  Fifth-order weights b
+ * (propagated), fourth-order weights bs (embedded estimate).  The solver of
+ * the paper's Julia comparison runs (Sec. 4.2).                              */
+static const double DP_c[7] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0};
+static const double DP_a[7][6] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0 / 5.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {3.0 / 40.0, 9.0 / 40.0, 0.0, 0.0, 0.0, 0.0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0.0, 0.0, 0.0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0.0, 0.0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0.0},
+    {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0}};
+static const double DP_b[7] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0,
+                               11.0 / 84.0, 0.0};
+static const double DP_bs[7] = {5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0,
+                                -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0};
+
+/* Export of the tableau for the order-condition tests: c[7], a[49] row-major
+ * (7x7, strictly lower), b[7], bs[7].                                        */
+void orc_dopri5_tableau(double *c, double *a, double *b, double *bs)
+{
+    for (int i = 0; i < 7; ++i) {
+        c[i] = DP_c[i];
+        b[i] = DP_b[i];
+        bs[i] = DP_bs[i];
+        for (int j = 0; j < 7; ++j) a[i * 7 + j] = (j < 6) ? DP_a[i][j] : 0.0;
+    }
+}
+
+/* One Dormand-Prince trial step from (t, y) with step h and k1 = f(t, y).
+ * Stages 2..7 as for Cash-Karp; the seventh stage's state is y5 itself (its
+ * coupling row is b), so y5 is that state and k7 = f(t + h, y5) is returned
+ * for reuse.  err = h sum (b_i - bs_i) k_i over the seven stages.            */
+static void dp_step(int sys, const double *p, int dim, double t, double h, const double *y,
+                    const double *k1, double *y5, double *err, double *k7)
+{
+    double k[7][ORC_MAXDIM], ys[ORC_MAXDIM];
+    for (int i = 0; i < dim; ++i) k[0][i] = k1[i];
+    for (int s = 1; s < 7; ++s) {
+        for (int i = 0; i < dim; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < s; ++j) acc = acc + DP_a[s][j] * k[j][i];
+            ys[i] = y[i] + h * acc;
+        }
+        rhs(sys, p, t + DP_c[s] * h, ys, k[s]);
+    }
+    for (int i = 0; i < dim; ++i) {
+        double se = 0.0;
+        for (int j = 0; j < 7; ++j) se = se + (DP_b[j] - DP_bs[j]) * k[j][i];
+        y5[i] = ys[i];
+        err[i] = h * se;
+        k7[i] = k[6][i];
+    }
+}
+
+void orc_dopri5_step(int sys, const double *p, double t, double h, const double *y, double *y5,
+                     double *err)
+{
+    double k1[ORC_MAXDIM], k7[ORC_MAXDIM];
+    const int dim = orc_dim(sys);
+    rhs(sys, p, t, y, k1);
+    dp_step(sys, p, dim, t, h, y, k1, y5, err, k7);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Step-size controller (the paper gives tolerances only, Sec. 4.2.1; this
  * reading is the standard elementary controller for an order-4/5 pair):
  *   sc_i = atol + rtol * max(|y_i|, |y5_i|)
@@ -419,7 +489,27 @@ typedef struct {
     double phase_len;       /* phase length in tau                      */
     double t0, t1;          /* time span (event mode) / phase start     */
     double acc_t_start;     /* event mode: y1 minimum recorded for t >= */
+    int32_t method;         /* ORC_CASHKARP or ORC_DOPRI5               */
 } orc_tol;
+
+enum { ORC_CASHKARP = 0, ORC_DOPRI5 = 1 };
+
+/* One trial of the selected pair.  Returns the number of right-hand-side
+ * evaluations it made; *k_next_valid tells whether k_next = f(t + h, y5)
+ * (Dormand-Prince only).                                                     */
+static int rk45_trial(const orc_tol *tol, int sys, const double *p, int dim, double t, double h,
+                      const double *y, const double *k1, double *y5, double *err, double *k_next,
+                      int *k_next_valid)
+{
+    if (tol->method == ORC_DOPRI5) {
+        dp_step(sys, p, dim, t, h, y, k1, y5, err, k_next);
+        *k_next_valid = 1;
+        return 6;
+    }
+    ck_step(sys, p, dim, t, h, y, k1, y5, err);
+    *k_next_valid = 0;
+    return 5;
+}
 
 static double err_norm(int dim, const double *y, const double *y5, const double *err,
                        const orc_tol *tol)
@@ -459,7 +549,7 @@ static void solve_phased(int sys, const double *p, int dim, double *y, double *d
                          int64_t *nacc, int64_t *nrej, int64_t *nrhs)
 {
     double dt = *dt_io;
-    double k1[ORC_MAXDIM], y5[ORC_MAXDIM], err[ORC_MAXDIM];
+    double k1[ORC_MAXDIM], y5[ORC_MAXDIM], err[ORC_MAXDIM], kn[ORC_MAXDIM];
     int64_t trials = 0, acc_steps = 0, rej_steps = 0, rhs_evals = 0;
     int st = 0;
     for (int ph = 0; ph < tol->n_phases; ++ph) {
@@ -472,16 +562,18 @@ static void solve_phased(int sys, const double *p, int dim, double *y, double *d
             int clamped = 0;
             if (trials >= tol->max_steps) { st |= ORC_ST_MAX_STEPS; break; }
             if (h >= tau_end - tau) { h = tau_end - tau; clamped = 1; }
+            int kn_valid;
             if (!k1_valid) { rhs(sys, p, tau, y, k1); rhs_evals += 1; k1_valid = 1; }
-            ck_step(sys, p, dim, tau, h, y, k1, y5, err);
-            rhs_evals += 5;
+            rhs_evals += rk45_trial(tol, sys, p, dim, tau, h, y, k1, y5, err, kn, &kn_valid);
             trials += 1;
             E = err_norm(dim, y, y5, err, tol);
             fac = step_factor(E);
             if (E <= 1.0) {
                 tau = clamped ? tau_end : tau + h;
-                for (int d = 0; d < dim; ++d) y[d] = y5[d];
-                k1_valid = 0;
+                for (int d = 0; d < dim; ++d) { y[d] = y5[d]; k1[d] = kn[d]; }
+                /* Dormand-Prince: k1 of the next step is f(tau + h, y5); a
+                 * phase end (the loop ends) restarts from f(t0, y)          */
+                k1_valid = kn_valid;
                 acc_steps += 1;
                 if (y[0] > ymax) ymax = y[0];
                 if (y[0] < ymin) ymin = y[0];
@@ -580,7 +672,7 @@ static void solve_events(int sys, const double *p, int dim, double *y, double *t
     const double beta = (sys == ORC_PRV) ? p[3] : 0.0;
     const double etol = tol->event_tol;
     double t = *t_io, dt = *dt_io, h_ev = 0.0;
-    double k1[ORC_MAXDIM], y5[ORC_MAXDIM], err[ORC_MAXDIM], yold[ORC_MAXDIM];
+    double k1[ORC_MAXDIM], y5[ORC_MAXDIM], err[ORC_MAXDIM], yold[ORC_MAXDIM], kn[ORC_MAXDIM];
     double ring[ORC_RING];
     double ymin = INFINITY;
     int64_t trials = 0, acc_steps = 0, rej_steps = 0, rhs_evals = 0, nmax = 0, nimp = 0;
@@ -609,9 +701,9 @@ static void solve_events(int sys, const double *p, int dim, double *y, double *t
         h = dt;
         if (h >= tol->t1 - t) { h = tol->t1 - t; limited = 1; }
         if (h_ev > 0.0 && h_ev < h) { h = h_ev; limited = 2; }
+        int kn_valid;
         if (!k1_valid) { rhs(sys, p, t, y, k1); rhs_evals += 1; k1_valid = 1; }
-        ck_step(sys, p, dim, t, h, y, k1, y5, err);
-        rhs_evals += 5;
+        rhs_evals += rk45_trial(tol, sys, p, dim, t, h, y, k1, y5, err, kn, &kn_valid);
         trials += 1;
         E = err_norm(dim, y, y5, err, tol);
         fac = step_factor(E);
@@ -640,9 +732,9 @@ static void solve_events(int sys, const double *p, int dim, double *y, double *t
             continue;
         }
         /* accept */
-        for (int d = 0; d < dim; ++d) { yold[d] = y[d]; y[d] = y5[d]; }
+        for (int d = 0; d < dim; ++d) { yold[d] = y[d]; y[d] = y5[d]; k1[d] = kn[d]; }
         t = (limited == 1) ? tol->t1 : t + h;
-        k1_valid = 0;
+        k1_valid = kn_valid;          /* Dormand-Prince: f(t + h, y5); cleared by an impact */
         acc_steps += 1;
         ev_retries = 0;
         h_ev = 0.0;
@@ -659,6 +751,7 @@ static void solve_events(int sys, const double *p, int dim, double *y, double *t
         if (fabs(y[0]) <= etol && y[1] < 0.0) {
             y[0] = 0.0;
             y[1] = -r * y[1];
+            k1_valid = 0;
             nimp += 1;
             if (sys == ORC_PRV) {
                 const double a = delta - y[2];
@@ -684,7 +777,8 @@ static void solve_events(int sys, const double *p, int dim, double *y, double *t
     *nrhs = rhs_evals;
 }
 
-/* Adaptive Cash-Karp ensemble solve.  Phase mode when tol->n_phases > 0 (the
+/* Adaptive ensemble solve with the pair tol->method selects (Cash-Karp or
+ * Dormand-Prince).  Phase mode when tol->n_phases > 0 (the
  * Keller-Miksis runs), event mode for ORC_PRV / ORC_BALL, otherwise plain
  * integration over [t0, t1] (the same controller, no events).
  * y: SoA [dim][n] in/out.  t_out, dt_out: final time and step proposal per

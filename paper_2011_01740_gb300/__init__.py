@@ -53,7 +53,8 @@ class EnsTol(ctypes.Structure):
                 ("event_tol", ctypes.c_double), ("max_steps", ctypes.c_int64),
                 ("n_steps", ctypes.c_int64), ("n_phases", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("phase_len", ctypes.c_double),
-                ("acc_t_start", ctypes.c_double), ("timeout_s", ctypes.c_double)]
+                ("acc_t_start", ctypes.c_double), ("timeout_s", ctypes.c_double),
+                ("n_transient", ctypes.c_int32)]
 
 
 class EnsLaunch(ctypes.Structure):
@@ -174,9 +175,9 @@ def _check(status: int, ctx=None):
 
 def make_tol(rtol=1e-10, atol=1e-10, dt0=1e-2, dt_min=1e-14, dt_max=1e-1, event_tol=1e-6,
              max_steps=2_000_000_000, n_steps=0, n_phases=0, prec=ENS_FP64, phase_len=1.0,
-             acc_t_start=0.0, timeout_s=600.0) -> EnsTol:
+             acc_t_start=0.0, timeout_s=600.0, n_transient=0) -> EnsTol:
     return EnsTol(rtol, atol, dt0, dt_min, dt_max, event_tol, int(max_steps), int(n_steps),
-                  int(n_phases), int(prec), phase_len, acc_t_start, timeout_s)
+                  int(n_phases), int(prec), phase_len, acc_t_start, timeout_s, int(n_transient))
 
 
 def make_launch(mode=ENS_LAUNCH_PERSISTENT, block=128, blocks_per_sm=2, use_graph=0,

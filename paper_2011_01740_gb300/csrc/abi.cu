@@ -208,6 +208,10 @@ ens_status check_tol(ens_ctx* c, ens_solver solver, ens_system sys, const ens_to
     set_err(c, "phase mode needs phase_len > 0");
     return ENS_EINVAL;
   }
+  if (t.n_transient < 0 || (t.n_phases > 0 ? t.n_transient >= t.n_phases : t.n_transient != 0)) {
+    set_err(c, "n_transient must satisfy 0 <= n_transient < n_phases (0 outside phase mode)");
+    return ENS_EINVAL;
+  }
   if (sys == ENS_SYS_RELIEF_VALVE && !(t.event_tol > 0.0)) {
     set_err(c, "the relief valve needs event_tol > 0");
     return ENS_EINVAL;
@@ -259,6 +263,7 @@ AdaptArgs adapt_args(ens_ctx* c) {
   a.acc_t_start = c->tol.acc_t_start;
   a.max_steps = c->tol.max_steps;
   a.n_phases = c->tol.n_phases;
+  a.n_transient = c->tol.n_transient;
   a.persistent = 0;
   a.timeout_ns = timeout_ns(c->tol);
   return a;
@@ -396,7 +401,7 @@ ens_status ens_create(ens_ctx** out, ens_system sys, int64_t n, const double* pa
   c->t0 = t_span[0];
   c->t1 = t_span[1];
   if (solver == ENS_RKCK45) {
-    if (tol->n_phases > 0) c->acc_rows = 2 * (int64_t)tol->n_phases;
+    if (tol->n_phases > 0) c->acc_rows = 2 * (int64_t)(tol->n_phases - tol->n_transient);
     else if (sys == ENS_SYS_RELIEF_VALVE) c->acc_rows = kPrvAccRows;
   }
   cudaError_t e = cudaGetDevice(&c->device);

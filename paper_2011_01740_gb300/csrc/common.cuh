@@ -93,6 +93,7 @@ struct AdaptArgs {
   double t0, t1, phase_len, acc_t_start;
   int64_t max_steps;
   int32_t n_phases;
+  int32_t n_transient;   // phases before this one are not recorded
   int32_t persistent;
   uint64_t timeout_ns;
 };

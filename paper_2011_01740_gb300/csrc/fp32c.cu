@@ -186,9 +186,9 @@ __global__ void __launch_bounds__(256) ck_phased_fp32c_kernel(AdaptArgs a) {
     ymax = ymin = y0v;
   };
   auto finish_system = [&](int64_t sys) {
-    for (int p = ph; p < a.n_phases; ++p) {
-      a.acc[(int64_t)(2 * p) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
-      a.acc[(int64_t)(2 * p + 1) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
+    for (int p = max(ph, a.n_transient); p < a.n_phases; ++p) {
+      a.acc[(int64_t)(2 * (p - a.n_transient)) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
+      a.acc[(int64_t)(2 * (p - a.n_transient) + 1) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
     }
     a.y[sys] = ff_to_d(y0v);
     a.y[a.n + sys] = ff_to_d(y1v);
@@ -217,8 +217,10 @@ __global__ void __launch_bounds__(256) ck_phased_fp32c_kernel(AdaptArgs a) {
     }
     if (st != 0) {
       if (ph < a.n_phases) {
-        a.acc[(int64_t)(2 * ph) * a.n + i] = ff_to_d(ymax);
-        a.acc[(int64_t)(2 * ph + 1) * a.n + i] = ff_to_d(ymin);
+        if (ph >= a.n_transient) {
+          a.acc[(int64_t)(2 * (ph - a.n_transient)) * a.n + i] = ff_to_d(ymax);
+          a.acc[(int64_t)(2 * (ph - a.n_transient) + 1) * a.n + i] = ff_to_d(ymin);
+        }
         ++ph;
       }
       sys_done = true;
@@ -314,8 +316,10 @@ __global__ void __launch_bounds__(256) ck_phased_fp32c_kernel(AdaptArgs a) {
           dt = dt < a.dt_min ? a.dt_min : dt;
         }
         if (!(tau < tau_end)) {
-          a.acc[(int64_t)(2 * ph) * a.n + i] = ff_to_d(ymax);
-          a.acc[(int64_t)(2 * ph + 1) * a.n + i] = ff_to_d(ymin);
+          if (ph >= a.n_transient) {
+            a.acc[(int64_t)(2 * (ph - a.n_transient)) * a.n + i] = ff_to_d(ymax);
+            a.acc[(int64_t)(2 * (ph - a.n_transient) + 1) * a.n + i] = ff_to_d(ymin);
+          }
           ++ph;
           if (ph >= a.n_phases) {
             sys_done = true;

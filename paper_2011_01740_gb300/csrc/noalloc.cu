@@ -105,7 +105,8 @@ extern "C" ens_status ens_solve_noalloc(ens_system sys, int64_t n, const double*
   if (!(tol->rtol > 0.0 || tol->atol > 0.0) || !(tol->dt0 > 0.0) || !(tol->dt_min > 0.0) ||
       !(tol->dt_max >= tol->dt_min) || tol->max_steps <= 0 ||
       (sys == ENS_SYS_RELIEF_VALVE && !(tol->event_tol > 0.0 && t_span[1] > t_span[0])) ||
-      (sys == ENS_SYS_KELLER_MIKSIS && !(tol->phase_len > 0.0)))
+      (sys == ENS_SYS_KELLER_MIKSIS && !(tol->phase_len > 0.0)) || tol->n_transient < 0 ||
+      (sys == ENS_SYS_KELLER_MIKSIS ? tol->n_transient >= tol->n_phases : tol->n_transient != 0))
     return fail(ENS_EINVAL, "ens_solve_noalloc: invalid tolerances or time span");
   if (n == 0) return ENS_OK;
   if (!on_device(params) || !on_device(y0) || !on_device(y) || !on_device(t_out) || !on_device(dt_out) ||
@@ -159,6 +160,7 @@ extern "C" ens_status ens_solve_noalloc(ens_system sys, int64_t n, const double*
   a.acc_t_start = tol->acc_t_start;
   a.max_steps = tol->max_steps;
   a.n_phases = tol->n_phases;
+  a.n_transient = tol->n_transient;
   a.timeout_ns = (uint64_t)((tol->timeout_s > 0.0 ? tol->timeout_s : 600.0) * 1e9);
 
   // the claim counter and the status OR must start at zero on every call

@@ -152,10 +152,10 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
     dk = d0;
   };
   auto finish_system = [&](int64_t sys) {
-    // phases that were not completed are marked NaN
-    for (int p = ph; p < a.n_phases; ++p) {
-      a.acc[(int64_t)(2 * p) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
-      a.acc[(int64_t)(2 * p + 1) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
+    // recorded phases that were not completed are marked NaN
+    for (int p = max(ph, a.n_transient); p < a.n_phases; ++p) {
+      a.acc[(int64_t)(2 * (p - a.n_transient)) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
+      a.acc[(int64_t)(2 * (p - a.n_transient) + 1) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) a.y[c * a.n + sys] = y[c];
@@ -182,8 +182,10 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
     if (st != 0) {
       // close the current phase with what it has, then retire the system
       if (ph < a.n_phases) {
-        a.acc[(int64_t)(2 * ph) * a.n + i] = ymax;
-        a.acc[(int64_t)(2 * ph + 1) * a.n + i] = ymin;
+        if (ph >= a.n_transient) {
+          a.acc[(int64_t)(2 * (ph - a.n_transient)) * a.n + i] = ymax;
+          a.acc[(int64_t)(2 * (ph - a.n_transient) + 1) * a.n + i] = ymin;
+        }
         ++ph;
       }
       sys_done = true;
@@ -219,8 +221,10 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
           dt = dt < a.dt_min ? a.dt_min : dt;
         }
         if (!(tau < tau_end)) {
-          a.acc[(int64_t)(2 * ph) * a.n + i] = ymax;
-          a.acc[(int64_t)(2 * ph + 1) * a.n + i] = ymin;
+          if (ph >= a.n_transient) {
+            a.acc[(int64_t)(2 * (ph - a.n_transient)) * a.n + i] = ymax;
+            a.acc[(int64_t)(2 * (ph - a.n_transient) + 1) * a.n + i] = ymin;
+          }
           ++ph;
           if (ph >= a.n_phases) {
             sys_done = true;

@@ -64,6 +64,19 @@ def test_create_rejects_bad_arguments_without_touching_a_device(ens):
     assert "rtol" in ens.ens_last_error(None)
 
 
+def test_transient_phase_count_is_validated(ens):
+    """n_transient: 0 <= n_transient < n_phases in phase mode, 0 otherwise;
+    checked before any device work."""
+    C = np.zeros((13, 1))
+    y0 = np.array([[1.0], [0.0]])
+    for nt, nph in ((4, 4), (-1, 4), (1, 0)):
+        with pytest.raises(ens.EnsError) as e:
+            ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, 1, C, y0, (0.0, 1.0), ens.ENS_RKCK45,
+                           ens.make_tol(n_phases=nph, n_transient=nt))
+        assert e.value.status == ens.ENS_EINVAL
+        assert "n_transient" in ens.ens_last_error(None)
+
+
 def test_null_context_calls_are_harmless(ens):
     L = ens.lib()
     assert L.ens_solve(None, None) == ens.ENS_EINVAL

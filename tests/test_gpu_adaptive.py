@@ -117,6 +117,32 @@ def test_persistent_refill_solves_every_system_as_the_plain_launch():
             assert np.array_equal(g[k], ref[k], equal_nan=True), (k, L.as_dict())
 
 
+@pytest.mark.parametrize("prec", [ens.ENS_FP64, ens.ENS_FP32_COMP])
+def test_transient_phases_are_integrated_but_not_recorded(prec):
+    """n_transient = 5 of 8 phases: the recorded rows are the last 3 phases of
+    the run that records all 8, bitwise, in both precisions."""
+    km = W.km(11, 13, n_phases=8)
+    kw = dict(prec=prec) if prec == ens.ENS_FP64 else dict(prec=prec, rtol=1e-8, atol=1e-8)
+    full = _km_gpu(km, **kw)
+    part = _km_gpu(km, n_transient=5, **kw)
+    assert full["acc"].shape[0] == 16 and part["acc"].shape[0] == 6
+    assert np.array_equal(part["acc"], full["acc"][10:], equal_nan=True)
+    for k in ("y", "nacc", "nrej", "status"):
+        assert np.array_equal(part[k], full[k], equal_nan=True), k
+
+
+def test_transient_phases_match_the_oracle():
+    """A paper-style run, transient phases then recorded ones (Sec. 4.2), on a
+    small grid: the recorded rows against the oracle's full record."""
+    km = W.km(6, 7, n_phases=12)
+    g = _km_gpu(km, n_transient=8)
+    Co = km_coeffs_oracle(km["phys"], km["liquid"])
+    r, well = _well_conditioned(oracle.KM, Co, km["y0"], oracle_tol_from(km["tol"]))
+    assert g["sync"] == ens.ENS_OK and well.mean() > 0.75
+    err = rel_err(g["acc"], r["acc"][16:])
+    assert np.all(err[well] < ACC_TOL), err[well].max()
+
+
 def test_km_graph_replays_and_set_inputs():
     km = W.km(9, 11, n_phases=2)
     C = km_coeffs_lib(km["phys"], km["liquid"])

@@ -232,3 +232,82 @@ def test_single_thread_call_leaves_the_thread_default_alone():
     y0 = np.array([[1.0, 2.0]])
     oracle.rk4_solve(oracle.LINEAR, np.array([[-1.0, -2.0]]), y0, 0.0, 0.01, 10, nthreads=1)
     assert oracle.max_threads() == before
+
+
+# ---------------------------------------------------------------------------
+# Dormand-Prince 5(4)
+# ---------------------------------------------------------------------------
+
+def test_dopri5_row_sums_and_first_same_as_last():
+    c, A, b, bs = oracle.dopri5_tableau()
+    np.testing.assert_allclose(A.sum(axis=1), c, rtol=0, atol=4e-16)
+    assert np.all(np.triu(A) == 0.0)
+    # the seventh stage sits at t + h with coupling row b: k7 = f(t + h, y5)
+    assert c[6] == 1.0 and np.array_equal(A[6, :6], b[:6]) and b[6] == 0.0
+
+
+def test_dopri5_fifth_order_weights():
+    c, A, b, bs = oracle.dopri5_tableau()
+    for k in range(1, 6):
+        for t in _trees(k):
+            assert abs(b @ _phi(t, A) - 1.0 / _gamma(t)) < 4e-15, (k, t)
+
+
+def test_dopri5_fourth_order_embedded_weights():
+    c, A, b, bs = oracle.dopri5_tableau()
+    for k in range(1, 5):
+        for t in _trees(k):
+            assert abs(bs @ _phi(t, A) - 1.0 / _gamma(t)) < 4e-15, (k, t)
+    miss = max(abs(bs @ _phi(t, A) - 1.0 / _gamma(t)) for t in _trees(5))
+    assert miss > 1e-5
+
+
+def test_dopri5_weights_are_the_nearest_doubles_of_rationals():
+    c, A, b, bs = oracle.dopri5_tableau()
+    for x in list(c) + list(A.ravel()) + list(b) + list(bs):
+        f = Fraction(x).limit_denominator(1 << 19)
+        assert float(f) == x
+
+
+def test_dopri5_quadrature_exactness_and_local_orders():
+    t0, h = 0.2, 0.5
+    y5, err = oracle.dopri5_step(oracle.TPOW, [4.0, 1.0], t0, h, [0.0])
+    assert abs(y5[0] - ((t0 + h) ** 5 - t0 ** 5) / 5) < 1e-16
+    assert abs(err[0]) > 1e-7
+    y5, err = oracle.dopri5_step(oracle.TPOW, [3.0, 1.0], t0, h, [0.0])
+    assert abs(y5[0] - ((t0 + h) ** 4 - t0 ** 4) / 4) < 1e-16
+    assert abs(err[0]) < 1e-16
+
+    def errs(hh):
+        y5, err = oracle.dopri5_step(oracle.LINEAR, [-1.0], 0.0, hh, [1.0])
+        return y5[0] - math.exp(-hh), (y5[0] - err[0]) - math.exp(-hh)
+    a5, a4 = errs(0.1)
+    b5, b4 = errs(0.05)
+    assert 55 < a5 / b5 < 72
+    assert 28 < a4 / b4 < 37
+
+
+def test_dopri5_controller_and_first_same_as_last_count():
+    """Work law tol^(-1/5), and 1 + 6 evaluations per trial: k1 of an
+    accepted step is the previous k7, and a rejected step keeps its k1."""
+    steps = []
+    for tv in (1e-6, 1e-8, 1e-10):
+        tol = oracle.make_tol(rtol=tv, atol=0.0, dt0=1e-3, dt_min=1e-14, dt_max=1.0, t0=0.0, t1=20.0,
+                              method=oracle.DOPRI5)
+        r = oracle.cashkarp_solve(oracle.LINEAR, [[1.0]], [[1.0]], tol)
+        steps.append(int(r["nacc"][0]))
+        assert abs(r["y"][0, 0] / math.exp(20.0) - 1.0) < 20 * tv
+        assert r["nrhs"][0] == 1 + 6 * (r["nacc"][0] + r["nrej"][0])
+    for s0, s1 in zip(steps, steps[1:]):
+        assert 100 ** 0.2 * 0.9 < s1 / s0 < 100 ** 0.2 * 1.1, steps
+
+
+def test_dopri5_phase_mode_restarts_k1_each_phase():
+    """Phase mode: tau resets at each phase start, so k1 = f(t0, y) is
+    evaluated there instead of reusing k7: 1 + 6 trials per phase."""
+    tol = oracle.make_tol(rtol=1e-9, atol=1e-9, dt0=1e-2, dt_min=1e-14, dt_max=0.1, n_phases=3,
+                          phase_len=1.0, t0=0.0, method=oracle.DOPRI5)
+    r = oracle.cashkarp_solve(oracle.LINEAR, [[-0.5]], [[1.0]], tol)
+    assert r["status"][0] == 0
+    assert r["nrhs"][0] == 3 + 6 * (r["nacc"][0] + r["nrej"][0])
+    assert abs(r["y"][0, 0] - math.exp(-1.5)) < 1e-8
