@@ -252,6 +252,8 @@ def run_ours(args):
     if rank == 0 and not args.quick:
         secondary = run_secondary(ens, torch, stream, dev)
         secondary["km_fp32c_vs_fp64_1024x1024"] = run_config4(ens, torch, stream, dev)
+        secondary["km_dopri5_362x362"] = run_dopri5(ens, torch, stream, dev, ctx, C_d, y0_d, km, tol, launch,
+                                                    total_ms / args.steps)
         secondary["km_surrogate_screen"] = run_screen(ens, torch, stream, dev, ctx, km, total_ms / args.steps,
                                                       steps_local / args.steps, args)
 
@@ -381,6 +383,45 @@ def run_screen(ens, torch, stream, dev, ctx, km, solve_ms, solve_steps, args):
     r["value"] = r["screen_points"] / r["screened_total_s"]
     r["unit"] = "points/s"
     return r
+
+
+def run_dopri5(ens, torch, stream, dev, ck_ctx, C_d, y0_d, km, tol, launch, ck_ms):
+    """The headline sweep with the Dormand-Prince pair (the solver of the
+    paper's Julia runs, Sec. 4.2) on the same launch: throughput and the
+    right-hand-side evaluations against the Cash-Karp run."""
+    n = km["phys"]["pA1"].size
+    ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, n, C_d, y0_d, (0.0, 1.0), ens.ENS_DOPRI5, tol)
+    try:
+        ens.ens_set_launch(ctx, launch)
+        ens.ens_solve(ctx, stream)                 # warm-up (also builds the graph)
+        ens.ens_sync(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ens.ens_solve(ctx, stream)
+        e1.record(stream)
+        st = ens.ens_sync(ctx)
+        ms = e0.elapsed_time(e1)
+        nacc = ens.ens_read(ctx, ens.ENS_NSTEPS)
+        nrej = ens.ens_read(ctx, ens.ENS_NREJ)
+        nrhs = ens.ens_read(ctx, ens.ENS_NRHS)
+        acc = ens.ens_read(ctx, ens.ENS_ACC)
+    finally:
+        ens.ens_destroy(ctx)
+    ck_nrhs = ens.ens_read(ck_ctx, ens.ENS_NRHS)
+    ck_acc = ens.ens_read(ck_ctx, ens.ENS_ACC)
+    ck_nacc = ens.ens_read(ck_ctx, ens.ENS_NSTEPS)
+    # per-period maxima of the two pairs on the non-chaotic systems: both meet
+    # the same tolerance, so they agree to about the global error
+    rel = np.abs(acc[0::2] - ck_acc[0::2]) / np.abs(ck_acc[0::2])
+    per_sys = np.nanmax(rel, axis=0)
+    return {"ms": ms, "status": st, "accepted_steps": float(nacc.sum()), "trials": float(nacc.sum() + nrej.sum()),
+            "value": float(nacc.sum()) / (ms / 1e3), "unit": "system-steps/s",
+            "rhs_evals": float(nrhs.sum()), "rhs_evals_cashkarp": float(ck_nrhs.sum()),
+            "rhs_ratio_cashkarp_over_dopri5": float(ck_nrhs.sum() / nrhs.sum()),
+            "accepted_steps_cashkarp": float(ck_nacc.sum()),
+            "time_ratio_dopri5_over_cashkarp": ms / ck_ms,
+            "acc_max_rel_diff_vs_cashkarp": {"median": float(np.median(per_sys)),
+                                             "p90": float(np.percentile(per_sys, 90))}}
 
 
 def run_secondary(ens, torch, stream, dev):

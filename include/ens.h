@@ -69,10 +69,13 @@ typedef enum {
     ENS_SYS_RELIEF_VALVE = 3
 } ens_system;
 
-/* Steppers: classic RK4 with fixed steps (Sec. 3, Sec. 4.1) and the adaptive
+/* Steppers: classic RK4 with fixed steps (Sec. 3, Sec. 4.1), the adaptive
  * Cash-Karp 4(5) pair with error control (Sec. 4.2.1, Sec. 4.3.1; tableau of
- * Cash & Karp, ACM TOMS 16(3), 1990). */
-typedef enum { ENS_RK4 = 0, ENS_RKCK45 = 1 } ens_solver;
+ * Cash & Karp, ACM TOMS 16(3), 1990), and the Dormand-Prince 5(4) pair of the
+ * paper's Julia runs (Sec. 4.2; Dormand & Prince, J. Comput. Appl. Math. 6,
+ * 1980) with the same controller, reusing its seventh stage as the next
+ * step's first (ENS_NRHS counts 6 per trial plus one per fresh start). */
+typedef enum { ENS_RK4 = 0, ENS_RKCK45 = 1, ENS_DOPRI5 = 2 } ens_solver;
 
 /* Arithmetic of the kernels.
  *   ENS_FP64         IEEE double with fused multiply-add (the default path).

@@ -220,8 +220,9 @@ ens_status check_tol(ens_ctx* c, ens_solver solver, ens_system sys, const ens_to
     set_err(c, "the relief valve runs in event mode (n_phases must be 0)");
     return ENS_ENOTSUP;
   }
-  if (t.prec == ENS_FP32_COMP && !(sys == ENS_SYS_KELLER_MIKSIS && t.n_phases > 0)) {
-    set_err(c, "ENS_FP32_COMP is implemented for the Keller-Miksis phase mode");
+  if (t.prec == ENS_FP32_COMP &&
+      !(sys == ENS_SYS_KELLER_MIKSIS && t.n_phases > 0 && solver == ENS_RKCK45)) {
+    set_err(c, "ENS_FP32_COMP is implemented for the Keller-Miksis phase mode with Cash-Karp");
     return ENS_ENOTSUP;
   }
   if (t.prec != ENS_FP64 && t.prec != ENS_FP32_COMP) {
@@ -265,6 +266,7 @@ AdaptArgs adapt_args(ens_ctx* c) {
   a.n_phases = c->tol.n_phases;
   a.n_transient = c->tol.n_transient;
   a.persistent = 0;
+  a.pair = c->solver == ENS_DOPRI5 ? kDormandPrince : kCashKarp;
   a.timeout_ns = timeout_ns(c->tol);
   return a;
 }
@@ -377,13 +379,13 @@ ens_status ens_create(ens_ctx** out, ens_system sys, int64_t n, const double* pa
     set_err(nullptr, "unknown system %d", (int)sys);
     return ENS_EINVAL;
   }
-  if (solver != ENS_RK4 && solver != ENS_RKCK45) {
+  if (solver != ENS_RK4 && solver != ENS_RKCK45 && solver != ENS_DOPRI5) {
     set_err(nullptr, "unknown solver %d", (int)solver);
     return ENS_EINVAL;
   }
   ens_status st = check_tol(nullptr, solver, sys, *tol);
   if (st != ENS_OK) return st;
-  if (solver == ENS_RKCK45 && tol->n_phases == 0 && !(t_span[1] > t_span[0])) {
+  if (solver != ENS_RK4 && tol->n_phases == 0 && !(t_span[1] > t_span[0])) {
     set_err(nullptr, "t_span[1] must exceed t_span[0]");
     return ENS_EINVAL;
   }
@@ -400,7 +402,7 @@ ens_status ens_create(ens_ctx** out, ens_system sys, int64_t n, const double* pa
   c->npar = sys_npar(sys);
   c->t0 = t_span[0];
   c->t1 = t_span[1];
-  if (solver == ENS_RKCK45) {
+  if (solver != ENS_RK4) {
     if (tol->n_phases > 0) c->acc_rows = 2 * (int64_t)(tol->n_phases - tol->n_transient);
     else if (sys == ENS_SYS_RELIEF_VALVE) c->acc_rows = kPrvAccRows;
   }

@@ -95,6 +95,7 @@ struct AdaptArgs {
   int32_t n_phases;
   int32_t n_transient;   // phases before this one are not recorded
   int32_t persistent;
+  int32_t pair;          // kCashKarp or kDormandPrince
   uint64_t timeout_ns;
 };
 
@@ -127,5 +128,27 @@ constexpr double bs1 = 2825.0 / 27648.0, bs3 = 18575.0 / 48384.0, bs4 = 13525.0 
                  bs5 = 277.0 / 14336.0, bs6 = 1.0 / 4.0;
 constexpr double d1 = b1 - bs1, d3 = b3 - bs3, d4 = b4 - bs4, d5 = -bs5, d6 = b6 - bs6;
 }  // namespace ck
+
+// Dormand & Prince (1980) 5(4) pair.  The seventh stage (c7 = 1) has the
+// fifth-order weights as its coupling row, so its state is the new solution
+// and k7 = f(t + h, y5) serves as the next step's k1 (first same as last).
+// e_i = b_i - bs_i are the weights of the embedded error estimate.
+namespace dp {
+constexpr double c2 = 1.0 / 5.0, c3 = 3.0 / 10.0, c4 = 4.0 / 5.0, c5 = 8.0 / 9.0;
+constexpr double a21 = 1.0 / 5.0;
+constexpr double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+constexpr double a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
+constexpr double a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0, a53 = 64448.0 / 6561.0,
+                 a54 = -212.0 / 729.0;
+constexpr double a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0, a64 = 49.0 / 176.0,
+                 a65 = -5103.0 / 18656.0;
+constexpr double b1 = 35.0 / 384.0, b3 = 500.0 / 1113.0, b4 = 125.0 / 192.0, b5 = -2187.0 / 6784.0,
+                 b6 = 11.0 / 84.0;
+constexpr double e1 = b1 - 5179.0 / 57600.0, e3 = b3 - 7571.0 / 16695.0, e4 = b4 - 393.0 / 640.0,
+                 e5 = b5 + 92097.0 / 339200.0, e6 = b6 - 187.0 / 2100.0, e7 = -1.0 / 40.0;
+}  // namespace dp
+
+// Embedded Runge-Kutta pair of the adaptive kernels.
+enum Pair : int { kCashKarp = 0, kDormandPrince = 1 };
 
 }  // namespace ens

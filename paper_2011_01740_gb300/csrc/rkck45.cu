@@ -77,6 +77,72 @@ __device__ __forceinline__ void ck_trial(const Sys& s, double t, double h, const
   }
 }
 
+// ---------------------------------------------------------------------------
+// one Dormand-Prince trial: stages 2..7 from k1.  The seventh stage's state is
+// y5 and k7 = f(t + h, y5) is returned for reuse as the next k1; stages 6
+// and 7 share the drive at t + h (returned in d7).
+// ---------------------------------------------------------------------------
+template <class Sys>
+__device__ __forceinline__ void dp_trial(const Sys& s, double t, double h, const double* y,
+                                         const double* k1, double* y5, double* err, double* k7,
+                                         typename Sys::Drive& d7) {
+  constexpr int D = Sys::kDim;
+  double k2[D], k3[D], k4[D], k5[D], k6[D], ys[D];
+  double ts;
+#pragma unroll
+  for (int c = 0; c < D; ++c) ys[c] = fma(h, dp::a21 * k1[c], y[c]);
+  ts = fma(dp::c2, h, t);
+  s.fd(s.drive(ts), ts, ys, k2);
+#pragma unroll
+  for (int c = 0; c < D; ++c) ys[c] = fma(h, fma(dp::a32, k2[c], dp::a31 * k1[c]), y[c]);
+  ts = fma(dp::c3, h, t);
+  s.fd(s.drive(ts), ts, ys, k3);
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+    ys[c] = fma(h, fma(dp::a43, k3[c], fma(dp::a42, k2[c], dp::a41 * k1[c])), y[c]);
+  ts = fma(dp::c4, h, t);
+  s.fd(s.drive(ts), ts, ys, k4);
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+    ys[c] = fma(h, fma(dp::a54, k4[c], fma(dp::a53, k3[c], fma(dp::a52, k2[c], dp::a51 * k1[c]))),
+                y[c]);
+  ts = fma(dp::c5, h, t);
+  s.fd(s.drive(ts), ts, ys, k5);
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+    ys[c] = fma(h,
+                fma(dp::a65, k5[c],
+                    fma(dp::a64, k4[c], fma(dp::a63, k3[c], fma(dp::a62, k2[c], dp::a61 * k1[c])))),
+                y[c]);
+  ts = t + h;  // c6 = c7 = 1
+  d7 = s.drive(ts);
+  s.fd(d7, ts, ys, k6);
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+    y5[c] = fma(h,
+                fma(dp::b6, k6[c],
+                    fma(dp::b5, k5[c], fma(dp::b4, k4[c], fma(dp::b3, k3[c], dp::b1 * k1[c])))),
+                y[c]);
+  s.fd(d7, ts, y5, k7);
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+    err[c] = h * fma(dp::e7, k7[c],
+                     fma(dp::e6, k6[c],
+                         fma(dp::e5, k5[c], fma(dp::e4, k4[c], fma(dp::e3, k3[c], dp::e1 * k1[c])))));
+}
+
+// One trial of the selected pair.  dn receives the drive at t + h; for
+// Dormand-Prince kn receives k7 = f(t + h, y5), the next k1 after acceptance.
+template <int PAIR, class Sys>
+__device__ __forceinline__ void pair_trial(const Sys& s, double t, double h, const double* y,
+                                           const double* k1, double* y5, double* err, double* kn,
+                                           typename Sys::Drive& dn) {
+  if (PAIR == kDormandPrince) dp_trial(s, t, h, y, k1, y5, err, kn, dn);
+  else ck_trial(s, t, h, y, k1, y5, err, dn);
+}
+// right-hand-side evaluations of one trial besides k1
+constexpr uint32_t pair_rhs(int PAIR) { return PAIR == kDormandPrince ? 6u : 5u; }
+
 template <int D>
 __device__ __forceinline__ double err_norm(const double* y, const double* y5, const double* err,
                                            double rtol, double atol) {
@@ -121,7 +187,7 @@ __device__ __forceinline__ int64_t claim(const AdaptArgs& a, bool first) {
 // tau in [t0, t0 + phase_len] with tau reset at each phase start; running max
 // and min of y1 over the accepted step points and the phase start.
 // ---------------------------------------------------------------------------
-template <class Sys>
+template <class Sys, int PAIR>
 __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
   constexpr int D = Sys::kDim;
   const double tau_end = a.t0 + a.phase_len;
@@ -131,7 +197,7 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
   Sys s;
   // drive at the phase start (tau = t0), at the current tau, and at tau + h
   typename Sys::Drive d0, dk, d5;
-  double y[D], k1[D], y5[D], err[D];
+  double y[D], k1[D], y5[D], err[D], kn[D];
   double tau = a.t0, dt = a.dt0, ymax = 0.0, ymin = 0.0;
   int32_t ph = 0, st = 0;
   uint32_t trials = 0, nacc = 0, nrej = 0, nrhs = 0, iter = 0;
@@ -201,17 +267,20 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
         ++nrhs;
         k1v = true;
       }
-      ck_trial(s, tau, h, y, k1, y5, err, d5);
-      nrhs += 5;
+      pair_trial<PAIR>(s, tau, h, y, k1, y5, err, kn, d5);
+      nrhs += pair_rhs(PAIR);
       ++trials;
       const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
       const double fac = step_factor(E);
       if (E <= 1.0) {
         tau = clamped ? tau_end : tau + h;
-        dk = d5;  // tau + h, the time of stage 5; a phase end below resets it
+        dk = d5;  // drive at tau + h; a phase end below resets it
 #pragma unroll
-        for (int c = 0; c < D; ++c) y[c] = y5[c];
-        k1v = false;
+        for (int c = 0; c < D; ++c) {
+          y[c] = y5[c];
+          if (PAIR == kDormandPrince) k1[c] = kn[c];
+        }
+        k1v = PAIR == kDormandPrince;  // k7 = f(tau + h, y5); a phase end below clears it
         ++nacc;
         ymax = fmax(ymax, y[0]);
         ymin = fmin(ymin, y[0]);
@@ -231,6 +300,7 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
           } else {
             tau = a.t0;
             dk = d0;
+            k1v = false;
             ymax = ymin = y[0];
           }
         }
@@ -285,6 +355,7 @@ __device__ __forceinline__ double event_frac(double g0, double d0, double g1, do
   return (den > 0.0 && x > 0.0 && x < 1.0) ? x : chord;
 }
 
+template <int PAIR>
 __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
   using Sys = ReliefValve;
   constexpr int D = Sys::kDim;
@@ -294,7 +365,7 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
   bool timed_out = false;
   Sys s;
   Sys::Drive d5;  // autonomous: empty
-  double y[D], k1[D], y5[D], err[D];
+  double y[D], k1[D], y5[D], err[D], kn[D];
   double t = a.t0, dt = a.dt0, h_ev = 0.0, ymin = 0.0;
   int32_t st = 0, ev_retries = 0;
   uint32_t trials = 0, nacc = 0, nrej = 0, nrhs = 0, nmax = 0, nimp = 0, iter = 0;
@@ -371,8 +442,8 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
         ++nrhs;
         k1v = true;
       }
-      ck_trial(s, t, h, y, k1, y5, err, d5);
-      nrhs += 5;
+      pair_trial<PAIR>(s, t, h, y, k1, y5, err, kn, d5);
+      nrhs += pair_rhs(PAIR);
       ++trials;
       const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
       const double fac = step_factor(E);
@@ -400,9 +471,12 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
         } else {
           const double y1_old = y[1];
 #pragma unroll
-          for (int c = 0; c < D; ++c) y[c] = y5[c];
+          for (int c = 0; c < D; ++c) {
+            y[c] = y5[c];
+            if (PAIR == kDormandPrince) k1[c] = kn[c];
+          }
           t = (limited == 1) ? a.t1 : t + h;
-          k1v = false;
+          k1v = PAIR == kDormandPrince;  // k7 = f(t + h, y5); the impact law clears it
           ++nacc;
           ev_retries = 0;
           h_ev = 0.0;
@@ -418,6 +492,7 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
           if (fabs(y[0]) <= etol && y[1] < 0.0) {  // impact law
             y[0] = 0.0;
             y[1] = -s.r * y[1];
+            k1v = false;
             ++nimp;
             const double push = s.delta - y[2];
             if (push > 0.0 && y[1] * y[1] <= 2.0 * push * etol) {
@@ -441,7 +516,7 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
 // ---------------------------------------------------------------------------
 // plain adaptive integration over [t0, t1] (no phases, no events)
 // ---------------------------------------------------------------------------
-template <class Sys>
+template <class Sys, int PAIR>
 __global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
   constexpr int D = Sys::kDim;
   const uint64_t deadline = global_ns() + a.timeout_ns;
@@ -449,7 +524,7 @@ __global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
   bool timed_out = false;
   Sys s;
   typename Sys::Drive dk, d5;  // drive at t and at t + h
-  double y[D], k1[D], y5[D], err[D];
+  double y[D], k1[D], y5[D], err[D], kn[D];
   double t = a.t0, dt = a.dt0;
   int32_t st = 0;
   uint32_t trials = 0, nacc = 0, nrej = 0, nrhs = 0, iter = 0;
@@ -498,8 +573,8 @@ __global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
         ++nrhs;
         k1v = true;
       }
-      ck_trial(s, t, h, y, k1, y5, err, d5);
-      nrhs += 5;
+      pair_trial<PAIR>(s, t, h, y, k1, y5, err, kn, d5);
+      nrhs += pair_rhs(PAIR);
       ++trials;
       const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
       const double fac = step_factor(E);
@@ -507,8 +582,11 @@ __global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
         t = clamped ? a.t1 : t + h;
         dk = d5;  // t + h; a clamped step ends the system
 #pragma unroll
-        for (int c = 0; c < D; ++c) y[c] = y5[c];
-        k1v = false;
+        for (int c = 0; c < D; ++c) {
+          y[c] = y5[c];
+          if (PAIR == kDormandPrince) k1[c] = kn[c];
+        }
+        k1v = PAIR == kDormandPrince;
         ++nacc;
         if (!clamped) {
           dt = h * fac;
@@ -546,46 +624,54 @@ struct AdaptFixed : Fixed {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_ck45(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s) {
-  if (a.n == 0) return cudaSuccess;
-  if (L.grid <= 0 || L.grid > 0x7fffffffLL || L.block <= 0) return cudaErrorInvalidConfiguration;
-  const dim3 g((unsigned)L.grid), b((unsigned)L.block);
+template <int PAIR>
+cudaError_t launch_pair(int sys, unsigned flags, const AdaptArgs& a, dim3 g, dim3 b, cudaStream_t s) {
   const bool dual = flags & kKmDual;
   const bool exp215 = !(flags & kKmGeneralExponent);
   if (a.n_phases > 0) {
     switch (sys) {
       case ENS_SYS_KELLER_MIKSIS:
         if (dual) {
-          if (exp215) ck_phased_kernel<KellerMiksis<true, true>><<<g, b, 0, s>>>(a);
-          else ck_phased_kernel<KellerMiksis<true, false>><<<g, b, 0, s>>>(a);
+          if (exp215) ck_phased_kernel<KellerMiksis<true, true>, PAIR><<<g, b, 0, s>>>(a);
+          else ck_phased_kernel<KellerMiksis<true, false>, PAIR><<<g, b, 0, s>>>(a);
         } else {
-          if (exp215) ck_phased_kernel<KellerMiksis<false, true>><<<g, b, 0, s>>>(a);
-          else ck_phased_kernel<KellerMiksis<false, false>><<<g, b, 0, s>>>(a);
+          if (exp215) ck_phased_kernel<KellerMiksis<false, true>, PAIR><<<g, b, 0, s>>>(a);
+          else ck_phased_kernel<KellerMiksis<false, false>, PAIR><<<g, b, 0, s>>>(a);
         }
         break;
-      case ENS_SYS_LORENZ: ck_phased_kernel<AdaptFixed<Lorenz>><<<g, b, 0, s>>>(a); break;
-      case ENS_SYS_TOY_X2P: ck_phased_kernel<AdaptFixed<X2P>><<<g, b, 0, s>>>(a); break;
+      case ENS_SYS_LORENZ: ck_phased_kernel<AdaptFixed<Lorenz>, PAIR><<<g, b, 0, s>>>(a); break;
+      case ENS_SYS_TOY_X2P: ck_phased_kernel<AdaptFixed<X2P>, PAIR><<<g, b, 0, s>>>(a); break;
       default: return cudaErrorInvalidValue;
     }
   } else if (sys == ENS_SYS_RELIEF_VALVE) {
-    ck_events_kernel<<<g, b, 0, s>>>(a);
+    ck_events_kernel<PAIR><<<g, b, 0, s>>>(a);
   } else {
     switch (sys) {
       case ENS_SYS_KELLER_MIKSIS:
         if (dual) {
-          if (exp215) ck_plain_kernel<KellerMiksis<true, true>><<<g, b, 0, s>>>(a);
-          else ck_plain_kernel<KellerMiksis<true, false>><<<g, b, 0, s>>>(a);
+          if (exp215) ck_plain_kernel<KellerMiksis<true, true>, PAIR><<<g, b, 0, s>>>(a);
+          else ck_plain_kernel<KellerMiksis<true, false>, PAIR><<<g, b, 0, s>>>(a);
         } else {
-          if (exp215) ck_plain_kernel<KellerMiksis<false, true>><<<g, b, 0, s>>>(a);
-          else ck_plain_kernel<KellerMiksis<false, false>><<<g, b, 0, s>>>(a);
+          if (exp215) ck_plain_kernel<KellerMiksis<false, true>, PAIR><<<g, b, 0, s>>>(a);
+          else ck_plain_kernel<KellerMiksis<false, false>, PAIR><<<g, b, 0, s>>>(a);
         }
         break;
-      case ENS_SYS_LORENZ: ck_plain_kernel<AdaptFixed<Lorenz>><<<g, b, 0, s>>>(a); break;
-      case ENS_SYS_TOY_X2P: ck_plain_kernel<AdaptFixed<X2P>><<<g, b, 0, s>>>(a); break;
+      case ENS_SYS_LORENZ: ck_plain_kernel<AdaptFixed<Lorenz>, PAIR><<<g, b, 0, s>>>(a); break;
+      case ENS_SYS_TOY_X2P: ck_plain_kernel<AdaptFixed<X2P>, PAIR><<<g, b, 0, s>>>(a); break;
       default: return cudaErrorInvalidValue;
     }
   }
   return cudaGetLastError();
+}
+
+// Adaptive launch with the pair a.pair selects (Cash-Karp or Dormand-Prince).
+cudaError_t launch_ck45(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  if (L.grid <= 0 || L.grid > 0x7fffffffLL || L.block <= 0) return cudaErrorInvalidConfiguration;
+  const dim3 g((unsigned)L.grid), b((unsigned)L.block);
+  if (a.pair == kDormandPrince) return launch_pair<kDormandPrince>(sys, flags, a, g, b, s);
+  if (a.pair != kCashKarp) return cudaErrorInvalidValue;
+  return launch_pair<kCashKarp>(sys, flags, a, g, b, s);
 }
 
 }  // namespace ens

@@ -246,7 +246,8 @@ def _prv_compare(g, r, well, idx=None):
 def test_prv_small_parity():
     wl = _prv(300, 64.0)
     g = _prv_gpu(wl)
-    r, well = _well_conditioned(oracle.PRV, wl["params"], wl["y0"], oracle_tol_from(wl["tol"]))
+    r, well = _well_conditioned(oracle.PRV, wl["params"], wl["y0"], oracle_tol_from(wl["tol"]),
+                                 rows=slice(0, 33))
     assert g["sync"] == ens.ENS_OK and np.all(g["status"] == 0)
     assert well.mean() > 0.75, well.mean()
     _prv_compare(g, r, well)
@@ -263,7 +264,8 @@ def test_prv_full_sweep_sampled_parity():
     assert g["sync"] == ens.ENS_OK
     idx = W.subsample(262144, 96)
     sub = W.take(wl, idx)
-    r, well = _well_conditioned(oracle.PRV, sub["params"], sub["y0"], oracle_tol_from(wl["tol"]))
+    r, well = _well_conditioned(oracle.PRV, sub["params"], sub["y0"], oracle_tol_from(wl["tol"]),
+                                 rows=slice(0, 33))
     assert well.mean() > 0.5, well.mean()
     _prv_compare(g, r, well, idx)
     # every valve: impacting below q ~ 7.5 (Sec. 4.3), pressure non-negative
