@@ -252,6 +252,7 @@ def run_ours(args):
     if rank == 0 and not args.quick:
         secondary = run_secondary(ens, torch, stream, dev)
         secondary["km_fp32c_vs_fp64_1024x1024"] = run_config4(ens, torch, stream, dev)
+        secondary["km_work_precision_16384f"] = run_work_precision(ens, torch, stream, dev)
         secondary["km_dopri5_362x362"] = run_dopri5(ens, torch, stream, dev, ctx, C_d, y0_d, km, tol, launch,
                                                     total_ms / args.steps)
         secondary["km_surrogate_screen"] = run_screen(ens, torch, stream, dev, ctx, km, total_ms / args.steps,
@@ -383,6 +384,49 @@ def run_screen(ens, torch, stream, dev, ctx, km, solve_ms, solve_steps, args):
     r["value"] = r["screen_points"] / r["screened_total_s"]
     r["unit"] = "points/s"
     return r
+
+
+def run_work_precision(ens, torch, stream, dev, m_f=16384):
+    """Tolerance-error-work study of Sec. 4.2.2 on a full ensemble: p_A = 1.5 bar,
+    m_f frequencies log-spaced over 20 kHz - 1 MHz, tau in [0, 2], both pairs
+    at T = 1e-6 ... 1e-12; the global error E = |y1(2) - y1^E(2)| is taken
+    against a Dormand-Prince run at T = 1e-14."""
+    km = W.km(1, m_f, n_phases=1, pa_max=1.5e5)
+    ph = km["phys"]
+    ph["pA1"][:] = 1.5e5
+    C = ens.ens_km_coefficients(ph["pA1"], ph["f1"], ph["pA2"], ph["f2"], ph["theta"], ph["RE"], km["liquid"])
+    launch = ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=160, blocks_per_sm=1, cost_order=1)
+
+    def solve(solver, T):
+        tol = ens.make_tol(rtol=T, atol=T, dt0=1e-2, dt_min=1e-14, dt_max=1e-1, timeout_s=600.0)
+        ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, m_f, C, km["y0"], (0.0, 2.0), solver, tol)
+        try:
+            ens.ens_set_launch(ctx, launch)
+            ens.ens_solve(ctx, stream)
+            ens.ens_sync(ctx)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ens.ens_solve(ctx, stream)
+            e1.record(stream)
+            st = ens.ens_sync(ctx)
+            return (ens.ens_read(ctx, ens.ENS_STATE)[0], float(ens.ens_read(ctx, ens.ENS_NRHS).sum()),
+                    float(ens.ens_read(ctx, ens.ENS_NSTEPS).sum()), e0.elapsed_time(e1), st)
+        finally:
+            ens.ens_destroy(ctx)
+
+    ref = solve(ens.ENS_DOPRI5, 1e-14)[0]
+    out = {"systems": m_f, "reference": "Dormand-Prince, T = 1e-14"}
+    for name, solver in (("cashkarp", ens.ENS_RKCK45), ("dopri5", ens.ENS_DOPRI5)):
+        rows = []
+        for k in (6, 8, 10, 12):
+            y, nrhs, nacc, ms, st = solve(solver, 10.0 ** -k)
+            E = np.abs(y - ref)
+            rows.append({"tol": 10.0 ** -k, "status": st, "ms": ms, "rhs_per_system": nrhs / m_f,
+                         "accepted_steps_per_s": nacc / (ms / 1e3),
+                         "E_median": float(np.median(E)), "E_p90": float(np.percentile(E, 90)),
+                         "E_max": float(E.max())})
+        out[name] = rows
+    return out
 
 
 def run_dopri5(ens, torch, stream, dev, ck_ctx, C_d, y0_d, km, tol, launch, ck_ms):
