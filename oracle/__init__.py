@@ -30,10 +30,10 @@ _lock = threading.Lock()
 _lib = None
 
 # system identifiers (mirror the enum in oracle.c)
-X2P, LORENZ, KM, PRV, LINEAR, TPOW, BALL = range(7)
+X2P, LORENZ, KM, PRV, LINEAR, TPOW, BALL, KM_TAN = range(8)
 CASHKARP, DOPRI5 = 0, 1                     # Tol.method
-DIM = {X2P: 1, LORENZ: 3, KM: 2, PRV: 3, LINEAR: 1, TPOW: 1, BALL: 3}
-NPAR = {X2P: 1, LORENZ: 3, KM: 13, PRV: 5, LINEAR: 1, TPOW: 2, BALL: 2}
+DIM = {X2P: 1, LORENZ: 3, KM: 2, PRV: 3, LINEAR: 1, TPOW: 1, BALL: 3, KM_TAN: 4}
+NPAR = {X2P: 1, LORENZ: 3, KM: 13, PRV: 5, LINEAR: 1, TPOW: 2, BALL: 2, KM_TAN: 13}
 
 ST_DT_UNDERFLOW, ST_MAX_STEPS, ST_NONFINITE, ST_EVENT_NO_CONVERGE = 1, 2, 4, 8
 RING = 32
@@ -221,7 +221,7 @@ def make_tol(rtol=1e-10, atol=1e-10, dt0=1e-2, dt_min=1e-14, dt_max=1e-1, event_
 
 def n_acc_rows(sys: int, tol: Tol) -> int:
     if tol.n_phases > 0:
-        return 2 * tol.n_phases
+        return (3 if sys == KM_TAN else 2) * tol.n_phases
     if sys in (PRV, BALL):
         return RING + 3
     return 0

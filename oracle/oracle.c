@@ -38,7 +38,7 @@
 #include <omp.h>
 #endif
 
-#define ORC_MAXDIM 3
+#define ORC_MAXDIM 4
 
 /* systems */
 enum {
@@ -48,7 +48,8 @@ enum {
     ORC_PRV = 3,      /* pressure relief valve           params: q,kappa,delta,beta,r */
     ORC_LINEAR = 4,   /* y' = lambda*y (test problem)    params: lambda            */
     ORC_TPOW = 5,     /* y' = c*t^k   (test problem)     params: k, c              */
-    ORC_BALL = 6      /* y1'=y2, y2'=-g, y3'=0 (test)    params: g, r              */
+    ORC_BALL = 6,     /* y1'=y2, y2'=-g, y3'=0 (test)    params: g, r              */
+    ORC_KM_TAN = 7    /* Keller-Miksis + tangent vector  params: C0..C12           */
 };
 
 /* per-system status bits */
@@ -69,6 +70,7 @@ int orc_dim(int sys)
     case ORC_LINEAR: return 1;
     case ORC_TPOW: return 1;
     case ORC_BALL: return 3;
+    case ORC_KM_TAN: return 4;
     default: return 0;
     }
 }
@@ -83,6 +85,7 @@ int orc_npar(int sys)
     case ORC_LINEAR: return 1;
     case ORC_TPOW: return 2;
     case ORC_BALL: return 2;
+    case ORC_KM_TAN: return 13;
     default: return 0;
     }
 }
@@ -135,6 +138,37 @@ static void rhs_km(const double *C, double tau, const double *y, double *dy)
     dy[1] = N / D;
 }
 
+/* Keller-Miksis with its tangent (variational) equation, for the largest
+ * Lyapunov exponent of each system.  y = (y1, y2, v1, v2): (y1, y2) follow
+ * rhs_km and v' = J v with J the Jacobian of that right-hand side, derived
+ * by hand from N_KM and D_KM (g = N_KM / D_KM, F_s and F_c the two forcing
+ * sums, P = (1/y1)^C10):
+ *   dN/dy1 = -C10 (C0 + C1 y2) P / y1 + C3 / y1^2 + C4 y2 / y1^2 - F_c
+ *   dN/dy2 = C1 P - C2 C9 - C4 / y1 - 3 y2 + (3/2) C9 y2^2 - C9 F_s
+ *   dD/dy1 = 1 - C9 y2,   dD/dy2 = -C9 y1
+ *   dg/dyk = (dN/dyk - g dD/dyk) / D
+ *   v1' = v2,   v2' = dg/dy1 v1 + dg/dy2 v2.                                */
+static void rhs_km_tan(const double *C, double tau, const double *y, double *dy)
+{
+    const double y1 = y[0], y2 = y[1];
+    const double pi2 = 2.0 * M_PI;
+    const double Fs = C[5] * sin(pi2 * tau) + C[6] * sin(pi2 * C[11] * tau + C[12]);
+    const double Fc = C[7] * cos(pi2 * tau) + C[8] * cos(pi2 * C[11] * tau + C[12]);
+    const double P = pow(1.0 / y1, C[10]);
+    double f[2], dNdy1, dNdy2, dDdy1, dDdy2, D, g;
+    rhs_km(C, tau, y, f);
+    D = y1 - C[9] * y1 * y2 + C[4] * C[9];
+    g = f[1];
+    dNdy1 = -C[10] * (C[0] + C[1] * y2) * P / y1 + C[3] / (y1 * y1) + C[4] * y2 / (y1 * y1) - Fc;
+    dNdy2 = C[1] * P - C[2] * C[9] - C[4] / y1 - 3.0 * y2 + 1.5 * C[9] * y2 * y2 - C[9] * Fs;
+    dDdy1 = 1.0 - C[9] * y2;
+    dDdy2 = -C[9] * y1;
+    dy[0] = f[0];
+    dy[1] = f[1];
+    dy[2] = y[3];
+    dy[3] = (dNdy1 - g * dDdy1) / D * y[2] + (dNdy2 - g * dDdy2) / D * y[3];
+}
+
 /* Pressure relief valve (Sec. 4.3, Eqs. pressure_relief_valve_1-3):
  *   y1' = y2,  y2' = -kappa y2 - (y1 + delta) + y3,  y3' = beta (q - y1 sqrt(y3)).
  * The pressure y3 stays non-negative for q > 0; sqrt is taken of max(y3, 0)
@@ -175,6 +209,7 @@ static void rhs(int sys, const double *p, double t, const double *y, double *dy)
     case ORC_X2P: rhs_x2p(p, t, y, dy); break;
     case ORC_LORENZ: rhs_lorenz(p, t, y, dy); break;
     case ORC_KM: rhs_km(p, t, y, dy); break;
+    case ORC_KM_TAN: rhs_km_tan(p, t, y, dy); break;
     case ORC_PRV: rhs_prv(p, t, y, dy); break;
     case ORC_LINEAR: rhs_linear(p, t, y, dy); break;
     case ORC_TPOW: rhs_tpow(p, t, y, dy); break;
@@ -543,7 +578,12 @@ static double step_factor(double E)
  * The step that would pass the phase end is shortened to end exactly on it;
  * when such a shortened step is accepted the step-size proposal dt is left as
  * it was, so the next phase starts from the unshortened proposal.  dt carries
- * over from phase to phase.                                                  */
+ * over from phase to phase.  For ORC_KM_TAN the tangent vector (v1, v2) is
+ * scaled to unit length at the start and at every phase end, and
+ * acc[(2 n_phases + k)*n + i] = ln |v| at the end of phase k (its growth over
+ * the phase): the mean of these rows over phases, divided by phase_len, is the
+ * largest Lyapunov exponent (Benettin's renormalisation between phases, the
+ * trajectory manipulation between phases that Sec. 1 describes).            */
 static void solve_phased(int sys, const double *p, int dim, double *y, double *dt_io,
                          const orc_tol *tol, int64_t n, int64_t i, double *acc, int32_t *status,
                          int64_t *nacc, int64_t *nrej, int64_t *nrhs)
@@ -552,6 +592,12 @@ static void solve_phased(int sys, const double *p, int dim, double *y, double *d
     double k1[ORC_MAXDIM], y5[ORC_MAXDIM], err[ORC_MAXDIM], kn[ORC_MAXDIM];
     int64_t trials = 0, acc_steps = 0, rej_steps = 0, rhs_evals = 0;
     int st = 0;
+    const int tangent = sys == ORC_KM_TAN;
+    if (tangent) {               /* the tangent vector starts at unit length */
+        const double nv = hypot(y[2], y[3]);
+        y[2] /= nv;
+        y[3] /= nv;
+    }
     for (int ph = 0; ph < tol->n_phases; ++ph) {
         const double tau_end = tol->t0 + tol->phase_len;
         double tau = tol->t0;
@@ -592,10 +638,19 @@ static void solve_phased(int sys, const double *p, int dim, double *y, double *d
             acc[(int64_t)(2 * ph) * n + i] = ymax;
             acc[(int64_t)(2 * ph + 1) * n + i] = ymin;
         }
+        if (tangent) {
+            /* renormalisation at the phase end (Benettin's method): the log of
+             * the tangent vector's growth over this phase, then unit length */
+            const double nv = hypot(y[2], y[3]);
+            if (acc) acc[(int64_t)(2 * tol->n_phases + ph) * n + i] = st ? NAN : log(nv);
+            y[2] /= nv;
+            y[3] /= nv;
+        }
         if (st) {
             for (int rest = ph + 1; rest < tol->n_phases && acc; ++rest) {
                 acc[(int64_t)(2 * rest) * n + i] = NAN;
                 acc[(int64_t)(2 * rest + 1) * n + i] = NAN;
+                if (tangent) acc[(int64_t)(2 * tol->n_phases + rest) * n + i] = NAN;
             }
             break;
         }

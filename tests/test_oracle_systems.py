@@ -121,6 +121,68 @@ def test_km_equilibrium_without_driving():
     assert np.abs(r["y"][0] - 1.0).max() < 1e-9
 
 
+def test_km_tangent_jacobian_matches_central_differences():
+    """The hand-derived Jacobian of the tangent system against central
+    differences of the plain Keller-Miksis right-hand side (random driven
+    states, both frequencies)."""
+    rng = np.random.default_rng(17)
+    n = 200
+    liq = _liq(WATER_CFG)
+    C = oracle.km_coefficients(rng.uniform(0, 2e5, n), rng.uniform(2e4, 1e6, n), rng.uniform(0, 1e5, n),
+                               rng.uniform(2e4, 2e6, n), rng.uniform(0, 6.28, n), 10e-6, liq)
+    y = np.stack([rng.uniform(0.3, 3.0, n), rng.uniform(-2.0, 2.0, n)])
+    tau = rng.uniform(0, 1, n)
+    for k in range(2):
+        v = np.zeros((2, n))
+        v[k] = 1.0
+        dt = oracle.rhs(oracle.KM_TAN, C, tau, np.vstack([y, v]))
+        h = 1e-6 * np.maximum(np.abs(y[k]), 1.0)
+        yp, ym = y.copy(), y.copy()
+        yp[k] += h
+        ym[k] -= h
+        fd = (oracle.rhs(oracle.KM, C, tau, yp)[1] - oracle.rhs(oracle.KM, C, tau, ym)[1]) / (2 * h)
+        scale = np.maximum(np.abs(fd), np.abs(oracle.rhs(oracle.KM, C, tau, y)[1]) / np.abs(y[k]).clip(1e-3))
+        assert np.all(np.abs(dt[3] - fd) <= 1e-6 * scale + 1e-9), k
+        # the state part is the plain right-hand side, the first tangent row v2
+        np.testing.assert_array_equal(dt[:2], oracle.rhs(oracle.KM, C, tau, y))
+        np.testing.assert_array_equal(dt[2], v[1])
+
+
+def test_km_lyapunov_exponent_of_the_rest_state():
+    """Unforced bubble at rest (P_A = 0, y = (1, 0)): the tangent equation is
+    v' = J v with J the (constant) Jacobian there.  The per-phase log growths
+    of the renormalised tangent vector add up to ln |exp(J k) v0| / |v0| after
+    k phases (matrix exponential, J by central differences of the plain RHS):
+    the renormalisation between phases loses nothing."""
+    from scipy.linalg import expm
+    liq = _liq(WATER_CFG)
+    f = np.array([2e4, 1e5, 5e5])
+    C = oracle.km_coefficients(0.0, f, 0.0, 0.0, 0.0, 10e-6, liq)
+    y0 = np.vstack([np.ones(3), np.zeros(3), np.ones(3), np.ones(3)])
+    tol = oracle.make_tol(rtol=1e-11, atol=1e-11, dt0=1e-2, dt_min=1e-14, dt_max=1e-1, n_phases=30,
+                          phase_len=1.0, t0=0.0)
+    r = oracle.cashkarp_solve(oracle.KM_TAN, C, y0, tol)
+    assert np.all(r["status"] == 0) and r["acc"].shape[0] == 90
+    growth = r["acc"][60:]                             # ln |v| per phase
+    for j in range(3):
+        J = np.zeros((2, 2))
+        for k in range(2):
+            yp = np.array([[1.0], [0.0]])
+            ym = yp.copy()
+            yp[k] += 1e-6
+            ym[k] -= 1e-6
+            Cj = C[:, j:j + 1]
+            J[:, k] = (oracle.rhs(oracle.KM, Cj, 0.0, yp) - oracle.rhs(oracle.KM, Cj, 0.0, ym))[:, 0] / 2e-6
+        lam = np.linalg.eigvals(J).real.max()
+        assert lam < 0                                  # the rest state is stable
+        v0 = np.array([1.0, 1.0]) / math.sqrt(2.0)
+        exact = np.array([math.log(np.linalg.norm(expm(J * k) @ v0)) for k in range(1, 31)])
+        np.testing.assert_allclose(np.cumsum(growth[:, j]), exact, rtol=1e-5, atol=1e-7)
+        # once the transient of the non-normal J has passed, the per-phase growth
+        # oscillates about lam (complex pair): the late mean is below zero
+        assert growth[15:, j].mean() < 0
+
+
 def test_km_dimensionless_form_equals_dimensional_equation():
     """y2' from C0..C12 equals R'' (2 pi / w1)^2 / R_E of the dimensional
     Keller-Miksis equation, including the dual-frequency terms."""
