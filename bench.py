@@ -253,6 +253,7 @@ def run_ours(args):
         secondary = run_secondary(ens, torch, stream, dev)
         secondary["km_fp32c_vs_fp64_1024x1024"] = run_config4(ens, torch, stream, dev)
         secondary["km_work_precision_16384f"] = run_work_precision(ens, torch, stream, dev)
+        secondary["km_lyapunov_362x362"] = run_lyapunov(ens, torch, stream, dev, C_d, km, launch)
         secondary["km_dopri5_362x362"] = run_dopri5(ens, torch, stream, dev, ctx, C_d, y0_d, km, tol, launch,
                                                     total_ms / args.steps)
         secondary["km_surrogate_screen"] = run_screen(ens, torch, stream, dev, ctx, km, total_ms / args.steps,
@@ -384,6 +385,42 @@ def run_screen(ens, torch, stream, dev, ctx, km, solve_ms, solve_steps, args):
     r["value"] = r["screen_points"] / r["screened_total_s"]
     r["unit"] = "points/s"
     return r
+
+
+def run_lyapunov(ens, torch, stream, dev, C_d, km, launch, n_phases=64, n_transient=32):
+    """Largest Lyapunov exponent over the headline sweep: the Keller-Miksis
+    tangent system, renormalised at every phase end on the device (Sec. 1,
+    trajectory manipulation between phases), exponent = mean of the recorded
+    per-phase log growths (phases 33-64) per unit tau."""
+    n = km["phys"]["pA1"].size
+    y0 = np.vstack([np.ones(n), np.zeros(n), np.ones(n), np.ones(n)])
+    t = km["tol"]
+    tol = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max, n_phases=n_phases,
+                       n_transient=n_transient, timeout_s=900.0)
+    ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS_TANGENT, n, C_d, torch.from_numpy(y0).to(dev), (0.0, 1.0),
+                         ens.ENS_RKCK45, tol)
+    try:
+        ens.ens_set_launch(ctx, launch)
+        ens.ens_solve(ctx, stream)
+        ens.ens_sync(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ens.ens_solve(ctx, stream)
+        e1.record(stream)
+        st = ens.ens_sync(ctx)
+        ms = e0.elapsed_time(e1)
+        acc = ens.ens_read(ctx, ens.ENS_ACC)
+        nacc = ens.ens_read(ctx, ens.ENS_NSTEPS)
+        kms = ens.ens_kernel_ms(ctx)
+    finally:
+        ens.ens_destroy(ctx)
+    R = n_phases - n_transient
+    lam = acc[2 * R:].mean(axis=0)                       # per unit tau (phase_len = 1)
+    forced = km["phys"]["pA1"] > 0
+    return {"ms": ms, "kernel_ms": kms, "status": st, "accepted_steps": float(nacc.sum()),
+            "value": float(nacc.sum()) / (ms / 1e3), "unit": "system-steps/s",
+            "chaotic_fraction": float(np.mean(lam[forced] > 0.0)),
+            "lambda_quantiles": {q: float(np.percentile(lam[forced], q)) for q in (5, 50, 95)}}
 
 
 def run_work_precision(ens, torch, stream, dev, m_f=16384):

@@ -61,12 +61,22 @@ typedef enum {
  *                          y3' = beta (q - y1 sqrt(y3))     (Sec. 4.3, Eqs.
  *                          pressure_relief_valve_1-3) with the impact law
  *                          y1 <- 0, y2 <- -r y2 (Eqs. impact_law_1-3);
- *                          dim 3, params [q, kappa, delta, beta, r]          */
+ *                          dim 3, params [q, kappa, delta, beta, r]
+ *   ENS_SYS_KELLER_MIKSIS_TANGENT
+ *                          Keller-Miksis with its tangent (variational)
+ *                          equation v' = J(y) v for the largest Lyapunov
+ *                          exponent; dim 4 (y1, y2, v1, v2), params as
+ *                          Keller-Miksis; phase mode only, FP64.  v is scaled
+ *                          to unit length at the start and at every phase end
+ *                          (renormalisation between phases, Sec. 1), and
+ *                          ln |v| at each recorded phase end is an extra
+ *                          accessory row (see ens_acc_rows).                */
 typedef enum {
     ENS_SYS_TOY_X2P = 0,
     ENS_SYS_LORENZ = 1,
     ENS_SYS_KELLER_MIKSIS = 2,
-    ENS_SYS_RELIEF_VALVE = 3
+    ENS_SYS_RELIEF_VALVE = 3,
+    ENS_SYS_KELLER_MIKSIS_TANGENT = 4
 } ens_system;
 
 /* Steppers: classic RK4 with fixed steps (Sec. 3, Sec. 4.1), the adaptive
@@ -227,6 +237,10 @@ ens_status ens_read(ens_ctx *ctx, int which, void *dst, size_t dst_bytes);
  *   phase mode (Keller-Miksis): 2 * (n_phases - n_transient), row 2k = max y1
  *     in phase n_transient + k, row 2k+1 = its min y1, taken over the natural
  *     step points and the phase start (no dense output, Sec. 4.2.1);
+ *   tangent system: 3 * R with R = n_phases - n_transient, the 2R rows above
+ *     and then row 2R + k = ln |v| at the end of recorded phase k (the
+ *     tangent vector's growth over that phase; their mean over phases divided
+ *     by phase_len estimates the largest Lyapunov exponent);
  *   relief valve: 35 rows: rows 0..31 ring of the last Poincare maxima of y1
  *     (slot m mod 32 holds maximum number m; NaN if unused), row 32 the
  *     minimum of y1 for t >= acc_t_start, row 33 the number of maxima, row 34

@@ -170,7 +170,7 @@ __global__ void km_flags_kernel(const double* C, int64_t n, unsigned* flags) {
 
 ens_status detect_flags(ens_ctx* c) {
   c->km_flags = 0;
-  if (c->sys != ENS_SYS_KELLER_MIKSIS || c->n == 0) return ENS_OK;
+  if (!is_km(c->sys) || c->n == 0) return ENS_OK;
   ENS_CUDA(c, cudaMemset(&c->scratch->any_status, 0, sizeof(unsigned)));
   const int64_t blocks = std::min<int64_t>((c->n + 255) / 256, 4096);
   km_flags_kernel<<<(unsigned)blocks, 256>>>(c->params, c->n, &c->scratch->any_status);
@@ -215,6 +215,10 @@ ens_status check_tol(ens_ctx* c, ens_solver solver, ens_system sys, const ens_to
   if (sys == ENS_SYS_RELIEF_VALVE && !(t.event_tol > 0.0)) {
     set_err(c, "the relief valve needs event_tol > 0");
     return ENS_EINVAL;
+  }
+  if (sys == ENS_SYS_KELLER_MIKSIS_TANGENT && !(t.n_phases > 0 && t.prec == ENS_FP64)) {
+    set_err(c, "the tangent system runs in phase mode (n_phases > 0) in FP64");
+    return ENS_ENOTSUP;
   }
   if (sys == ENS_SYS_RELIEF_VALVE && t.n_phases > 0) {
     set_err(c, "the relief valve runs in event mode (n_phases must be 0)");
@@ -265,6 +269,7 @@ AdaptArgs adapt_args(ens_ctx* c) {
   a.max_steps = c->tol.max_steps;
   a.n_phases = c->tol.n_phases;
   a.n_transient = c->tol.n_transient;
+  a.acc_phases = c->tol.n_phases - c->tol.n_transient;
   a.persistent = 0;
   a.pair = c->solver == ENS_DOPRI5 ? kDormandPrince : kCashKarp;
   a.timeout_ns = timeout_ns(c->tol);
@@ -403,7 +408,8 @@ ens_status ens_create(ens_ctx** out, ens_system sys, int64_t n, const double* pa
   c->t0 = t_span[0];
   c->t1 = t_span[1];
   if (solver != ENS_RK4) {
-    if (tol->n_phases > 0) c->acc_rows = 2 * (int64_t)(tol->n_phases - tol->n_transient);
+    if (tol->n_phases > 0)
+      c->acc_rows = (sys == ENS_SYS_KELLER_MIKSIS_TANGENT ? 3 : 2) * (int64_t)(tol->n_phases - tol->n_transient);
     else if (sys == ENS_SYS_RELIEF_VALVE) c->acc_rows = kPrvAccRows;
   }
   cudaError_t e = cudaGetDevice(&c->device);
@@ -469,7 +475,7 @@ ens_status ens_set_inputs(ens_ctx* c, const double* params, const double* y0, vo
     ENS_CUDA(c, cudaMemcpyAsync(c->params, params, nn * c->npar * sizeof(double), cudaMemcpyDefault, s));
   if (y0) ENS_CUDA(c, cudaMemcpyAsync(c->y0, y0, nn * c->dim * sizeof(double), cudaMemcpyDefault, s));
   c->last_stream = s;
-  if (params && c->sys == ENS_SYS_KELLER_MIKSIS) {
+  if (params && is_km(c->sys)) {
     ENS_CUDA(c, cudaStreamSynchronize(s));
     const unsigned was = c->km_flags;
     ens_status st = detect_flags(c);
@@ -684,7 +690,7 @@ ens_status ens_eval_rhs(ens_system sys, int64_t n, const double* params, const d
   if (!params || !t || !y || !dy) return ENS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned flags = 0;
-  if (sys == ENS_SYS_KELLER_MIKSIS) {
+  if (is_km(sys)) {
     unsigned* f = nullptr;
     if (cudaMalloc(&f, sizeof(unsigned)) != cudaSuccess) return ENS_ENOMEM;
     cudaMemsetAsync(f, 0, sizeof(unsigned), s);

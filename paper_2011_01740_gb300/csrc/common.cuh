@@ -35,9 +35,13 @@ inline int sys_dim(int sys) {
     case ENS_SYS_LORENZ: return 3;
     case ENS_SYS_KELLER_MIKSIS: return 2;
     case ENS_SYS_RELIEF_VALVE: return 3;
+    case ENS_SYS_KELLER_MIKSIS_TANGENT: return 4;
     default: return 0;
   }
 }
+
+// Systems whose parameters are the Keller-Miksis coefficients C0..C12.
+inline bool is_km(int sys) { return sys == ENS_SYS_KELLER_MIKSIS || sys == ENS_SYS_KELLER_MIKSIS_TANGENT; }
 
 inline int sys_npar(int sys) {
   switch (sys) {
@@ -45,6 +49,7 @@ inline int sys_npar(int sys) {
     case ENS_SYS_LORENZ: return 3;
     case ENS_SYS_KELLER_MIKSIS: return 13;
     case ENS_SYS_RELIEF_VALVE: return 5;
+    case ENS_SYS_KELLER_MIKSIS_TANGENT: return 13;
     default: return 0;
   }
 }
@@ -94,6 +99,8 @@ struct AdaptArgs {
   int64_t max_steps;
   int32_t n_phases;
   int32_t n_transient;   // phases before this one are not recorded
+  int32_t acc_phases;    // recorded phases of the accessory layout (rows of per-phase hooks follow
+                         // the 2 acc_phases max / min rows)
   int32_t persistent;
   int32_t pair;          // kCashKarp or kDormandPrince
   uint64_t timeout_ns;

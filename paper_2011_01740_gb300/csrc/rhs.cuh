@@ -24,6 +24,7 @@ __device__ __forceinline__ double smul(double a, double b) { return __dmul_rn(a,
 struct X2P {
   static constexpr int kDim = 1;
   static constexpr int kPar = 1;
+  static constexpr int kPhaseRows = 0;  // no per-phase hook
   double p;
   __device__ __forceinline__ void load(const double* P, int64_t n, int64_t i) { p = P[i]; }
   template <bool STRICT>
@@ -41,6 +42,7 @@ struct X2P {
 struct Lorenz {
   static constexpr int kDim = 3;
   static constexpr int kPar = 3;
+  static constexpr int kPhaseRows = 0;
   double rho, sigma, b;
   __device__ __forceinline__ void load(const double* P, int64_t n, int64_t i) {
     rho = P[i];
@@ -183,6 +185,7 @@ template <bool DUAL, bool EXP215 = false>
 struct KellerMiksis {
   static constexpr int kDim = 2;
   static constexpr int kPar = 13;
+  static constexpr int kPhaseRows = 0;
   double C0, C1, C2, C3, C4, C5, C6, C7, C8, C9, C10, C11, C12f, C4C9;
   struct Drive {
     double fs, fc;  // C5 sin 2 pi tau + C6 sin(...), C7 cos 2 pi tau + C8 cos(...)
@@ -215,31 +218,36 @@ struct KellerMiksis {
     }
     return d;
   }
-  __device__ __forceinline__ void fd(const Drive& d, double tau, const double* y, double* dy) const {
-    (void)tau;
-    const double y1 = y[0], y2 = y[1];
+  // y2' = N_KM / D_KM for a scalar type T: double, or the Dual of dual.cuh
+  // (the same operations then also carry a directional derivative).
+  template <class T>
+  __device__ __forceinline__ T accel(const Drive& d, T y1, T y2) const {
     // one reciprocal serves both 1/y1 and 1/D: w = 1 / (y1 D), 1/y1 = D w, N/D = N y1 w
-    const double D = fma(-C9 * y1, y2, y1) + C4C9;
-    const double w = rcp_nr(y1 * D);
-    const double rx = D * w;
-    double g;
+    const T D = fma(-C9 * y1, y2, y1) + C4C9;
+    const T w = rcp_nr(y1 * D);
+    const T rx = D * w;
+    T g;
     if (EXP215) {
-      const double rx2 = rx * rx;
+      const T rx2 = rx * rx;
       g = (rx2 * rx2) * inv_fifth_root(y1);
     } else {
       g = pow(rx, C10);
     }
-    const double one_c9y2 = fma(C9, y2, 1.0);
+    const T one_c9y2 = fma(C9, y2, 1.0);
     // (1 - C9 y2 / 3) * 1.5 * y2^2 = (1.5 - 0.5 C9 y2) y2^2
-    const double kin = fma(-0.5 * C9, y2, 1.5) * (y2 * y2);
-    double N = fma(C1, y2, C0) * g;
+    const T kin = fma(-0.5 * C9, y2, 1.5) * (y2 * y2);
+    T N = fma(C1, y2, C0) * g;
     N = fma(-C2, one_c9y2, N);
     N = fma(-fma(C4, y2, C3), rx, N);
     N -= kin;
     N = fma(-d.fs, one_c9y2, N);
     N = fma(-y1, d.fc, N);
-    dy[0] = y2;
-    dy[1] = N * (y1 * w);
+    return N * (y1 * w);
+  }
+  __device__ __forceinline__ void fd(const Drive& d, double tau, const double* y, double* dy) const {
+    (void)tau;
+    dy[0] = y[1];
+    dy[1] = accel<double>(d, y[0], y[1]);
   }
   __device__ __forceinline__ void f(double tau, const double* y, double* dy) const {
     fd(drive(tau), tau, y, dy);
@@ -255,6 +263,7 @@ struct KellerMiksis {
 struct ReliefValve {
   static constexpr int kDim = 3;
   static constexpr int kPar = 5;
+  static constexpr int kPhaseRows = 0;
   double q, kappa, delta, beta, r;
   __device__ __forceinline__ void load(const double* P, int64_t n, int64_t i) {
     q = P[i];

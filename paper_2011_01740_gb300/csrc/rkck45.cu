@@ -25,6 +25,7 @@
 // Loops are bounded: max_steps trials per system, 40 event retries in a row,
 // and a wall-clock budget read from %globaltimer; there are no spin-waits.
 #include "common.cuh"
+#include "dual.cuh"
 #include "rhs.cuh"
 
 namespace ens {
@@ -185,7 +186,9 @@ __device__ __forceinline__ int64_t claim(const AdaptArgs& a, bool first) {
 // ---------------------------------------------------------------------------
 // Phase mode (Keller-Miksis, Sec. 4.2): n_phases integrations over
 // tau in [t0, t0 + phase_len] with tau reset at each phase start; running max
-// and min of y1 over the accepted step points and the phase start.
+// and min of y1 over the accepted step points and the phase start.  Systems
+// with kPhaseRows (the tangent system) also run their phase_hook at the start
+// and at every phase end, recording its value in a row after the max / min.
 // ---------------------------------------------------------------------------
 template <class Sys, int PAIR>
 __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
@@ -216,12 +219,16 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
     ymax = ymin = y[0];
     d0 = s.drive(a.t0);
     dk = d0;
+    if constexpr (Sys::kPhaseRows > 0) s.phase_hook(y);   // tangent vector to unit length
   };
+  // per-phase hook row of recorded phase p (after the 2 acc_phases max / min rows)
+  auto hook_row = [&](int p) { return (int64_t)(2 * a.acc_phases + p - a.n_transient) * a.n; };
   auto finish_system = [&](int64_t sys) {
     // recorded phases that were not completed are marked NaN
     for (int p = max(ph, a.n_transient); p < a.n_phases; ++p) {
       a.acc[(int64_t)(2 * (p - a.n_transient)) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
       a.acc[(int64_t)(2 * (p - a.n_transient) + 1) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
+      if constexpr (Sys::kPhaseRows > 0) a.acc[hook_row(p) + sys] = __longlong_as_double(0x7ff8000000000000LL);
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) a.y[c * a.n + sys] = y[c];
@@ -251,6 +258,7 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
         if (ph >= a.n_transient) {
           a.acc[(int64_t)(2 * (ph - a.n_transient)) * a.n + i] = ymax;
           a.acc[(int64_t)(2 * (ph - a.n_transient) + 1) * a.n + i] = ymin;
+          if constexpr (Sys::kPhaseRows > 0) a.acc[hook_row(ph) + i] = __longlong_as_double(0x7ff8000000000000LL);
         }
         ++ph;
       }
@@ -293,6 +301,11 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
           if (ph >= a.n_transient) {
             a.acc[(int64_t)(2 * (ph - a.n_transient)) * a.n + i] = ymax;
             a.acc[(int64_t)(2 * (ph - a.n_transient) + 1) * a.n + i] = ymin;
+          }
+          if constexpr (Sys::kPhaseRows > 0) {
+            // renormalise the tangent vector between phases and record its growth
+            const double gr = s.phase_hook(y);
+            if (ph >= a.n_transient) a.acc[hook_row(ph) + i] = gr;
           }
           ++ph;
           if (ph >= a.n_phases) {
@@ -639,6 +652,15 @@ cudaError_t launch_pair(int sys, unsigned flags, const AdaptArgs& a, dim3 g, dim
           else ck_phased_kernel<KellerMiksis<false, false>, PAIR><<<g, b, 0, s>>>(a);
         }
         break;
+      case ENS_SYS_KELLER_MIKSIS_TANGENT:
+        if (dual) {
+          if (exp215) ck_phased_kernel<KellerMiksisTangent<true, true>, PAIR><<<g, b, 0, s>>>(a);
+          else ck_phased_kernel<KellerMiksisTangent<true, false>, PAIR><<<g, b, 0, s>>>(a);
+        } else {
+          if (exp215) ck_phased_kernel<KellerMiksisTangent<false, true>, PAIR><<<g, b, 0, s>>>(a);
+          else ck_phased_kernel<KellerMiksisTangent<false, false>, PAIR><<<g, b, 0, s>>>(a);
+        }
+        break;
       case ENS_SYS_LORENZ: ck_phased_kernel<AdaptFixed<Lorenz>, PAIR><<<g, b, 0, s>>>(a); break;
       case ENS_SYS_TOY_X2P: ck_phased_kernel<AdaptFixed<X2P>, PAIR><<<g, b, 0, s>>>(a); break;
       default: return cudaErrorInvalidValue;
@@ -704,6 +726,15 @@ cudaError_t launch_rhs_eval(int sys, unsigned flags, int64_t n, const double* P,
     case ENS_SYS_TOY_X2P: rhs_eval_kernel<AdaptFixed<X2P>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy); break;
     case ENS_SYS_LORENZ: rhs_eval_kernel<AdaptFixed<Lorenz>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy); break;
     case ENS_SYS_RELIEF_VALVE: rhs_eval_kernel<ReliefValve><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy); break;
+    case ENS_SYS_KELLER_MIKSIS_TANGENT:
+      if (dual) {
+        if (exp215) rhs_eval_kernel<KellerMiksisTangent<true, true>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy);
+        else rhs_eval_kernel<KellerMiksisTangent<true, false>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy);
+      } else {
+        if (exp215) rhs_eval_kernel<KellerMiksisTangent<false, true>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy);
+        else rhs_eval_kernel<KellerMiksisTangent<false, false>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy);
+      }
+      break;
     case ENS_SYS_KELLER_MIKSIS:
       if (dual) {
         if (exp215) rhs_eval_kernel<KellerMiksis<true, true>><<<(unsigned)blocks, 256, 0, s>>>(n, P, t, y, dy);

@@ -1,0 +1,122 @@
+"""GPU parity of the Keller-Miksis tangent system (ENS_SYS_KELLER_MIKSIS_TANGENT):
+the tangent equation from Dual evaluation against the oracle's hand-derived
+Jacobian, the per-phase renormalisation rows (Sec. 1: trajectory manipulation
+between phases, here for the largest Lyapunov exponent) against the oracle,
+and against the matrix exponential at the rest state."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2011_01740_gb300 as ens
+from paper_2011_01740_gb300 import workloads as W
+from gpu_helpers import ens_tol_from, km_coeffs_lib, km_coeffs_oracle, oracle_tol_from, rel_err, solve_gpu
+
+pytestmark = pytest.mark.gpu
+
+TAN = ens.ENS_SYS_KELLER_MIKSIS_TANGENT
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    ens.lib()
+
+
+def _eval(sys, params, t, y):
+    import torch
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    dy = torch.empty(y.shape, dtype=torch.float64, device="cuda")
+    ens.ens_eval_rhs(sys, t.size, dev(params), dev(t), dev(y), dy)
+    torch.cuda.synchronize()
+    return dy.cpu().numpy()
+
+
+def _tangent_y0(n, seed=3):
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=(2, n))
+    return np.vstack([np.ones(n), np.zeros(n), v])
+
+
+def test_tangent_rhs_matches_the_hand_derived_jacobian():
+    """J v by Dual evaluation (GPU) against the oracle's analytic Jacobian at
+    random driven states, both frequencies; the state rows equal the plain
+    Keller-Miksis right-hand side of the same library."""
+    rng = np.random.default_rng(23)
+    n = 4000
+    phys = dict(pA1=rng.uniform(0, 2e5, n), f1=rng.uniform(2e4, 1e6, n), pA2=rng.uniform(0, 1e5, n),
+                f2=rng.uniform(2e4, 2e6, n), theta=rng.uniform(0, 6.28, n), RE=np.full(n, 10e-6))
+    C = ens.ens_km_coefficients(phys["pA1"], phys["f1"], phys["pA2"], phys["f2"], phys["theta"], phys["RE"],
+                                W.WATER_25C)
+    y = np.vstack([rng.uniform(0.3, 3.0, n), rng.uniform(-2.0, 2.0, n), rng.normal(size=(2, n))])
+    t = rng.uniform(0, 1, n)
+    g = _eval(TAN, C, t, y)
+    plain = _eval(ens.ENS_SYS_KELLER_MIKSIS, C, t, y[:2])
+    np.testing.assert_array_equal(g[:2], plain)
+    np.testing.assert_array_equal(g[2], y[3])
+    o = oracle.rhs(oracle.KM_TAN, km_coeffs_oracle(phys, W.WATER_25C), t, y)
+    # scale of the terms that cancel in J v: |J| |v| with |J| bounded by the
+    # magnitude of the acceleration over the state
+    scale = (np.abs(o[3]) + np.abs(plain[1]) / np.minimum(np.abs(y[0]), 1.0) * np.abs(y[2:]).sum(0)
+             + np.abs(y[2:]).sum(0))
+    assert np.all(np.abs(g[3] - o[3]) <= 1e-12 * scale), np.max(np.abs(g[3] - o[3]) / scale)
+
+
+def test_rest_state_growth_matches_the_matrix_exponential():
+    """P_A = 0 at rest: v' = J v with constant J, so the recorded growths of
+    phases k0+1 .. k add up to ln |exp(J k) v0| - ln |exp(J k0) v0|."""
+    from scipy.linalg import expm
+    f = np.array([2e4, 1e5, 5e5])
+    z = np.zeros(3)
+    C = ens.ens_km_coefficients(z, f, z, z, z, np.full(3, 10e-6), W.WATER_25C)
+    y0 = np.vstack([np.ones(3), np.zeros(3), np.ones(3), np.ones(3)])
+    tol = ens.make_tol(rtol=1e-11, atol=1e-11, dt0=1e-2, dt_min=1e-14, dt_max=1e-1, n_phases=24, n_transient=4)
+    g = solve_gpu(TAN, C, y0, (0.0, 1.0), ens.ENS_RKCK45, tol)
+    assert g["sync"] == ens.ENS_OK and g["acc"].shape[0] == 60
+    growth = g["acc"][40:]
+    Co = C
+    v0 = np.array([1.0, 1.0]) / math.sqrt(2.0)
+    for j in range(3):
+        J = np.zeros((2, 2))
+        for k in range(2):
+            yp = np.array([[1.0], [0.0]])
+            ym = yp.copy()
+            yp[k] += 1e-6
+            ym[k] -= 1e-6
+            J[:, k] = (oracle.rhs(oracle.KM, Co[:, j:j + 1], 0.0, yp)
+                       - oracle.rhs(oracle.KM, Co[:, j:j + 1], 0.0, ym))[:, 0] / 2e-6
+        lg = [math.log(np.linalg.norm(expm(J * k) @ v0)) for k in range(4, 25)]
+        exact = np.array(lg[1:]) - lg[0]
+        np.testing.assert_allclose(np.cumsum(growth[:, j]), exact, rtol=1e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("solver,method", [(ens.ENS_RKCK45, oracle.CASHKARP), (ens.ENS_DOPRI5, oracle.DOPRI5)])
+def test_phase_mode_parity_with_transient(solver, method):
+    km = W.km(12, 14, n_phases=8)
+    n = km["phys"]["pA1"].size
+    C = km_coeffs_lib(km["phys"], km["liquid"])
+    Co = km_coeffs_oracle(km["phys"], km["liquid"])
+    y0 = _tangent_y0(n)
+    t = km["tol"]
+    g = solve_gpu(TAN, C, y0, (t.t0, t.t1), solver, ens_tol_from(t, n_transient=3))
+    assert g["sync"] == ens.ENS_OK and np.all(g["status"] == 0) and g["acc"].shape[0] == 15
+    otol = oracle_tol_from(t, method=method)
+    r = oracle.cashkarp_solve(oracle.KM_TAN, Co, y0, otol)
+    # well-conditioned: insensitive to 1e-14 state perturbations and to a
+    # 1e-12 relative shift of the first step
+    well = r["status"] == 0
+    shifted = oracle.make_tol(**{f: getattr(otol, f) for f, _ in otol._fields_})
+    shifted.dt0 = otol.dt0 * (1 + 1e-12)
+    for b in (oracle.cashkarp_solve(oracle.KM_TAN, Co, y0 * (1 + 1e-14), otol),
+              oracle.cashkarp_solve(oracle.KM_TAN, Co, y0 * (1 - 3e-15), otol),
+              oracle.cashkarp_solve(oracle.KM_TAN, Co, y0, shifted)):
+        well &= (rel_err(b["acc"][:16], r["acc"][:16]) < 1e-9) & (np.abs(b["acc"][16:] - r["acc"][16:]).max(0) < 1e-9)
+    assert well.mean() > 0.8, well.mean()
+    # value rows: oracle records every phase, the GPU phases 3..7
+    assert np.all(rel_err(g["acc"][:10], r["acc"][6:16])[well] < 1e-8)
+    d = np.abs(g["acc"][10:] - r["acc"][16 + 3:]).max(0)
+    assert np.all(d[well] < 1e-8), d[well].max()
+    # the final tangent vector has unit length (renormalised at the last phase end)
+    assert np.allclose(np.hypot(g["y"][2], g["y"][3]), 1.0, rtol=1e-14, atol=0)
