@@ -114,8 +114,19 @@ def test_phase_mode_parity_with_transient(solver, method):
               oracle.cashkarp_solve(oracle.KM_TAN, Co, y0, shifted)):
         well &= (rel_err(b["acc"][:16], r["acc"][:16]) < 1e-9) & (np.abs(b["acc"][16:] - r["acc"][16:]).max(0) < 1e-9)
     assert well.mean() > 0.8, well.mean()
+    # The per-phase max / min is sampled at the natural step points, so it is
+    # unique only for a given step sequence.  Including the tangent vector in
+    # the error test makes its estimate a small difference of large stage
+    # terms; rounding then flips a rare accept / reject decision between the
+    # two implementations (a few systems of the 168).  The value rows are
+    # compared where the step sequences agree (same accepted and rejected
+    # counts); the state and the growth rows, which do not depend on where
+    # the steps land, on every well-conditioned system.
+    same = well & (g["nacc"] == r["nacc"]) & (g["nrej"] == r["nrej"])
+    assert same.sum() >= 0.9 * well.sum(), (same.sum(), well.sum())
     # value rows: oracle records every phase, the GPU phases 3..7
-    assert np.all(rel_err(g["acc"][:10], r["acc"][6:16])[well] < 1e-8)
+    assert np.all(rel_err(g["acc"][:10], r["acc"][6:16])[same] < 1e-8)
+    assert np.all(rel_err(g["y"], r["y"])[well] < 1e-8)
     d = np.abs(g["acc"][10:] - r["acc"][16 + 3:]).max(0)
     assert np.all(d[well] < 1e-8), d[well].max()
     # the final tangent vector has unit length (renormalised at the last phase end)
