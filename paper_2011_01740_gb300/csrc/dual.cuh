@@ -38,6 +38,9 @@ __device__ __forceinline__ Dual fma(Dual a, Dual b, Dual c) {
 __device__ __forceinline__ Dual fma(double a, Dual b, Dual c) { return {fma(a, b.v, c.v), fma(a, b.d, c.d)}; }
 __device__ __forceinline__ Dual fma(double a, Dual b, double c) { return {fma(a, b.v, c), a * b.d}; }
 __device__ __forceinline__ Dual fma(Dual a, double b, Dual c) { return {fma(a.v, b, c.v), fma(a.d, b, c.d)}; }
+__device__ __forceinline__ Dual fma(Dual a, Dual b, double c) {
+  return {fma(a.v, b.v, c), fma(a.d, b.v, a.v * b.d)};
+}
 
 // (1/x)' = -x' / x^2 = -r^2 x'
 __device__ __forceinline__ Dual rcp_nr(Dual x) {

@@ -200,7 +200,7 @@ struct KellerMiksis {
   static constexpr int kDim = 2;
   static constexpr int kPar = 13;
   static constexpr int kPhaseRows = 0;
-  double C0, C1, C2, C3, C4, C5, C6, C7, C8, C9, C10, C11, C12f, C4C9;
+  double C0, C1, C2, C3, C4, C5, C6, C7, C8, C9, C10, C11, C12f, C4C9, C9h;
   struct Drive {
     double fs, fc;  // C5 sin 2 pi tau + C6 sin(...), C7 cos 2 pi tau + C8 cos(...)
   };
@@ -219,6 +219,7 @@ struct KellerMiksis {
     C11 = P[11 * n + i];
     C12f = P[12 * n + i] * (0.5 / 3.141592653589793238462643383279502884);  // C12 in turns
     C4C9 = C4 * C9;
+    C9h = -0.5 * C9;
   }
   __device__ __forceinline__ Drive drive(double tau) const {
     double s1, c1;
@@ -236,8 +237,9 @@ struct KellerMiksis {
   // (the same operations then also carry a directional derivative).
   template <class T>
   __device__ __forceinline__ T accel(const Drive& d, T y1, T y2) const {
-    // one reciprocal serves both 1/y1 and 1/D: w = 1 / (y1 D), 1/y1 = D w, N/D = N y1 w
-    const T D = fma(-C9 * y1, y2, y1) + C4C9;
+    // one reciprocal serves both 1/y1 and 1/D: w = 1 / (y1 D), 1/y1 = D w, N/D = N y1 w;
+    // D = y1 (1 - C9 y2) + C4 C9
+    const T D = fma(y1, fma(-C9, y2, 1.0), C4C9);
     const T w = rcp_nr(y1 * D);
     const T rx = D * w;
     T g;
@@ -248,12 +250,11 @@ struct KellerMiksis {
       g = pow(rx, C10);
     }
     const T one_c9y2 = fma(C9, y2, 1.0);
-    // (1 - C9 y2 / 3) * 1.5 * y2^2 = (1.5 - 0.5 C9 y2) y2^2
-    const T kin = fma(-0.5 * C9, y2, 1.5) * (y2 * y2);
     T N = fma(C1, y2, C0) * g;
     N = fma(-C2, one_c9y2, N);
     N = fma(-fma(C4, y2, C3), rx, N);
-    N -= kin;
+    // - (1 - C9 y2 / 3) * 1.5 * y2^2 = - (1.5 - 0.5 C9 y2) y2^2
+    N = fma(-fma(C9h, y2, 1.5), y2 * y2, N);
     N = fma(-d.fs, one_c9y2, N);
     N = fma(-y1, d.fc, N);
     return N * (y1 * w);

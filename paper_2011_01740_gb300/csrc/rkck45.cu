@@ -151,7 +151,9 @@ __device__ __forceinline__ double err_norm(const double* y, const double* y5, co
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     const double sc = fma(rtol, fmax(fabs(y[c]), fabs(y5[c])), atol);
-    const double r = fabs(err[c]) / sc;
+    // rcp_nr is within 1 ulp of 1/sc for the normal, finite sc of a solve; a
+    // zero, subnormal or infinite sc (blown-up trial) gives NaN: rejected
+    const double r = fabs(err[c]) * rcp_nr(sc);
     if (isnan(r)) E = r;
     else if (r > E) E = r;   // E stays NaN once NaN: NaN > r comparisons are false
   }
