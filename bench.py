@@ -34,14 +34,14 @@ from paper_2011_01740_gb300 import workloads as W  # noqa: E402
 # the Keller-Miksis kernel, and per RK4 step of the x' = x^2 - p and Lorenz
 # kernels, from the ncu instruction counters of profiles/ (None until
 # measured: the roofline then reports achieved = null).
-FLOPS_PER_KM_TRIAL = 624.88  # 239.64 DFMA + 129.65 DMUL + 15.95 DADD per trial (profiles/)
+FLOPS_PER_KM_TRIAL = 604.90  # 237.61 DFMA + 121.70 DMUL + 7.98 DADD per trial (profiles/)
 # all FP64 thread instructions per trial (DFMA, DMUL, DADD, compares, min/max),
 # for the FP64 pipe's instruction-issue fraction
-FP64_INST_PER_KM_TRIAL = 403.13
+FP64_INST_PER_KM_TRIAL = 384.20
 # DRAM bytes (read + write) of one benchmarked Keller-Miksis launch, from the
 # one-pass ncu capture in profiles/ (inputs 15.7 MB read once, 134 MB of
 # per-period accessories written once); None once the kernel changes.
-KM_LAUNCH_DRAM_BYTES = 38349824 + 120676352
+KM_LAUNCH_DRAM_BYTES = 39364096 + 121385216
 FLOPS_PER_X2P_STEP = 21.0     # 10 DFMA + 1 DADD (Sec. 3.2.2 counters; kernel counted by ncu)
 FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast kernel
 
