@@ -11,8 +11,13 @@
 //          acceptance test |err_i| <= atol + rtol max(|y_i|, |y5_i|)
 //          (err_i and the scale come from float quantities; the comparison
 //          and the tolerances are double).
-// The step factor 0.9 E^(-1/5) only scales the next proposal and is formed
-// in FP32.
+// The step factor s E^(-1/5) only scales the next proposal and is formed in
+// FP32, with the safety factor s = 0.8 (the FP64 kernels use 0.9).  This
+// variant runs at loose tolerances (1e-7, 1e-8), where the Keller-Miksis
+// collapses make the step proposal overshoot often: on the 1024 x 1024 sweep
+// at 1e-8, 26 % of the trials were rejected with 0.9 and 7.9 % with 0.8,
+// which ran 7 % faster with slightly smaller errors (0.7: 2.8 %, but 12 %
+// slower again).
 //
 // Stage sums use a compensated dot product (Ogita, Rump & Oishi, "Accurate
 // sum and dot product", SIAM J. Sci. Comput. 26, 2005: TwoProduct via fma and
@@ -34,6 +39,8 @@
 namespace ens {
 
 namespace {
+
+constexpr float kSafety = 0.8f;  // step-factor safety (see the header)
 
 struct ff {
   float hi, lo;
@@ -300,7 +307,7 @@ __global__ void __launch_bounds__(256) ck_phased_fp32c_kernel(AdaptArgs a) {
         float l, r;
         asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(Ec));
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-0.2f * l));
-        fac = fminf(fmaxf(0.9f * r, 0.2f), 5.0f);
+        fac = fminf(fmaxf(kSafety * r, 0.2f), 5.0f);
       }
       if (accept) {
         tau = clamped ? tau_end : tau + h;
