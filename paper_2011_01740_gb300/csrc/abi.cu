@@ -292,6 +292,8 @@ AdaptLaunch adapt_launch(const ens_ctx* c, const ens_launch& L) {
 
 // Enqueue one solve (no graph).  `L` is the launch to use; `shorten` > 0 runs
 // a reduced problem for tuning and planning (phases / horizon / steps cut).
+constexpr double kPilotTol = 1e-7;  // loosest tolerance of the claim-order pilot
+
 ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int shorten) {
   ENS_CUDA(c, cudaMemsetAsync(c->scratch, 0, sizeof(Scratch), s));
   if (c->solver == ENS_RK4) {
@@ -325,11 +327,17 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int sh
   a.persistent = L.mode == ENS_LAUNCH_PERSISTENT;
   if (a.persistent && L.cost_order && shorten == 0) {
     // pilot: one phase (or 1/16 of the horizon) of every system in plain
-    // mode, then order systems by decreasing pilot step count
+    // mode, then order systems by decreasing pilot step count.  The pilot
+    // only ranks the systems, so it runs at a tolerance of at least 1e-7: a
+    // quarter of the steps of a 1e-10 pilot, and on the 362 x 362
+    // Keller-Miksis sweep a whole solve 1.4 % faster with the same results
+    // (the claim order never changes what a system computes).
     AdaptArgs p = a;
     p.persistent = 0;
     if (p.n_phases > 0) p.n_phases = 1;
     else p.t1 = p.t0 + (p.t1 - p.t0) / 16.0;
+    p.rtol = p.rtol > kPilotTol ? p.rtol : kPilotTol;
+    p.atol = p.atol > kPilotTol ? p.atol : kPilotTol;
     AdaptLaunch PL{(c->n + 127) / 128, 128};
     cudaError_t e = c->tol.prec == ENS_FP32_COMP ? launch_ck45_fp32c(c->km_flags, p, PL, s)
                                                  : launch_ck45(c->sys, c->km_flags, p, PL, s);
