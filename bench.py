@@ -259,6 +259,13 @@ def run_ours(args):
         secondary["km_surrogate_screen"] = run_screen(ens, torch, stream, dev, ctx, km, total_ms / args.steps,
                                                       steps_local / args.steps, args)
 
+    # the same kernel-level rate against the FP64 rate this GPU reached on the
+    # x' = x^2 - p calibration kernel (10 DFMA + 1 DADD per step, Sec. 3)
+    cal = secondary.get("x2p_rk4_calibration")
+    if cal and roofline["achieved"]:
+        roofline["calibration_tflops"] = cal["fp64_tflops"]
+        roofline["frac_of_calibration"] = roofline["achieved"] / cal["fp64_tflops"]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(km, args.cpu_seconds)
