@@ -32,6 +32,7 @@ struct ens_mlp {
   float* out = nullptr;
   float* dout = nullptr;
   float* loss = nullptr;          // [members]
+  float* gpart = nullptr;         // [kMaxSplits][members][kP] partial gradients of the batch slices
   // screening on the tcgen05 tensor cores
   int screen_impl = 1;            // 1: tcgen05 kernel, 0: mma.sync fused kernel
   float* screen_out = nullptr;    // [members][screen_cap][2]
@@ -93,6 +94,8 @@ ens_status ensure_batch(ens_mlp* m, int64_t B) {
   if (e == cudaSuccess) e = cudaMalloc(&m->dz, M * 4 * B * mlp::H * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->out, M * B * 2 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->dout, M * B * 2 * sizeof(float));
+  if (e == cudaSuccess && !m->gpart)
+    e = cudaMalloc(&m->gpart, (size_t)mlp::kMaxSplits * M * mlp::kP * sizeof(float));
   if (e != cudaSuccess) {
     merr(m, "batch scratch: %s", cudaGetErrorString(e));
     return ENS_ENOMEM;
@@ -130,8 +133,11 @@ ens_status batch_grad(ens_mlp* m, int64_t B, float* loss, cudaStream_t s) {
   g.z = m->z;
   g.dz = m->dz;
   g.dout = m->dout;
-  g.grad = m->grad;
-  MLP_CUDA(m, mlp::launch_wgrad(g, m->members, s));
+  g.grad = m->gpart;
+  const int splits = mlp::grad_splits(B);
+  g.rows = ((B + splits - 1) / splits + mlp::kChunk - 1) / mlp::kChunk * mlp::kChunk;
+  MLP_CUDA(m, mlp::launch_wgrad(g, m->members, splits, s));
+  MLP_CUDA(m, mlp::launch_grad_reduce(m->members, splits, m->gpart, m->grad, s));
   return ENS_OK;
 }
 
@@ -503,6 +509,7 @@ void ens_mlp_destroy(ens_mlp* m) {
   cudaFree(m->m2);
   cudaFree(m->grad);
   cudaFree(m->loss);
+  cudaFree(m->gpart);
   cudaFree(m->xb);
   cudaFree(m->yb);
   cudaFree(m->z);

@@ -269,19 +269,24 @@ __global__ void __launch_bounds__(kThreads) mlp_backward_kernel(BwdArgs a) {
 
 
 
-// Weight and bias gradients.  grid = (members, 5): y = layer - 1.  Layers 2..4
+// Weight and bias gradients.  grid = (members, 5, slices): y = layer - 1,
+// z = batch slice of a.rows samples; each block writes the slice's partial
+// gradient (the slices are summed in order by mlp_grad_reduce).  Layers 2..4
 // on the tensor cores (dW[out][in] = sum_b dz[b][out] h[b][in], K = batch),
 // layers 1 and 5 in FP32.
 __global__ void __launch_bounds__(kThreads) mlp_wgrad_kernel(GradArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = blockIdx.x, l = blockIdx.y + 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  float* G = a.grad + (int64_t)m * kP;
+  float* G = a.grad + ((int64_t)blockIdx.z * gridDim.x + m) * kP;
   float* part = reinterpret_cast<float*>(smem);  // reduction scratch
+  const int64_t r0 = (int64_t)blockIdx.z * a.rows;
+  const int64_t r1 = r0 + a.rows < a.n ? r0 + a.rows : a.n;
   if (l == 1 || l == 5) {
-    // thread = (feature f, half of the batch)
+    // thread = (feature f, half of the slice)
     const int f = tid & (H - 1), half = tid >> 7;
-    const int64_t b0 = half * (a.n / 2), b1 = half ? a.n : a.n / 2;
+    const int64_t mid = r0 + (r1 - r0) / 2;
+    const int64_t b0 = half ? mid : r0, b1 = half ? r1 : mid;
     float s0 = 0.f, s1 = 0.f, sb = 0.f;
     if (l == 1) {
       for (int64_t b = b0; b < b1; ++b) {
@@ -330,13 +335,13 @@ __global__ void __launch_bounds__(kThreads) mlp_wgrad_kernel(GradArgs a) {
 #pragma unroll
   for (int nt = 0; nt < 16; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
   float bsum = 0.f;  // bias gradient partial of feature tid % 128
-  for (int64_t c0 = 0; c0 < a.n; c0 += kChunk) {
+  for (int64_t c0 = r0; c0 < r1; c0 += kChunk) {
     __syncthreads();
     for (int idx = tid; idx < kChunk * H; idx += kThreads) {
       const int bk = idx / H, f = idx % H;
       const int64_t b = c0 + bk;
       float d = 0.f, h = 0.f;
-      if (b < a.n) {
+      if (b < r1) {
         d = a.dz[(((int64_t)m * 4 + (l - 1)) * a.n + b) * H + f];
         h = gelu(a.z[(((int64_t)m * a.n + b) * 4 + (l - 2)) * H + f]);
       }
@@ -449,8 +454,24 @@ cudaError_t launch_backward(const BwdArgs& a, int members, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_wgrad(const GradArgs& a, int members, cudaStream_t s) {
-  mlp_wgrad_kernel<<<dim3(members, 5), kThreads, kGradSmem, s>>>(a);
+cudaError_t launch_wgrad(const GradArgs& a, int members, int splits, cudaStream_t s) {
+  if (splits < 1 || splits > kMaxSplits || a.rows % kChunk != 0 || (int64_t)splits * a.rows < a.n)
+    return cudaErrorInvalidValue;
+  mlp_wgrad_kernel<<<dim3(members, 5, splits), kThreads, kGradSmem, s>>>(a);
+  return cudaGetLastError();
+}
+
+__global__ void mlp_grad_reduce_kernel(int64_t total, int splits, const float* part, float* grad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    float acc = part[i];
+    for (int k = 1; k < splits; ++k) acc += part[(int64_t)k * total + i];
+    grad[i] = acc;
+  }
+}
+
+cudaError_t launch_grad_reduce(int members, int splits, const float* part, float* grad, cudaStream_t s) {
+  const int64_t total = (int64_t)members * kP;
+  mlp_grad_reduce_kernel<<<grid_1d(total), 256, 0, s>>>(total, splits, part, grad);
   return cudaGetLastError();
 }
 

@@ -58,21 +58,32 @@ struct BwdArgs {
   float* loss;        // [members] (sum over samples of the per-sample loss)
 };
 
+constexpr int kMaxSplits = 8;     // batch slices of the weight-gradient kernel
+
 struct GradArgs {
   int64_t n;
   const float* x;     // [n][2]
   const float* z;     // [members][n][4][128]
   const float* dz;    // [members][4][n][128]
   const float* dout;  // [members][n][2]
-  float* grad;        // [members][kP]
+  float* grad;        // [splits][members][kP]: one partial gradient per batch slice
+  int64_t rows;       // samples per slice (a multiple of kChunk)
 };
+
+// batch slices for n samples: one per 128 samples, at most kMaxSplits
+inline int grad_splits(int64_t n) {
+  const int64_t s = (n + 127) / 128;
+  return (int)(s < 1 ? 1 : (s > kMaxSplits ? kMaxSplits : s));
+}
 
 // Host launchers (the kernels live in mlp.cu).
 cudaError_t set_smem_limits();
 cudaError_t launch_forward_train(const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_forward_screen(const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_backward(const BwdArgs& a, int members, cudaStream_t s);
-cudaError_t launch_wgrad(const GradArgs& a, int members, cudaStream_t s);
+cudaError_t launch_wgrad(const GradArgs& a, int members, int splits, cudaStream_t s);
+// grad[m][i] = sum over slices of part[s][m][i], slices in order (deterministic)
+cudaError_t launch_grad_reduce(int members, int splits, const float* part, float* grad, cudaStream_t s);
 cudaError_t launch_adam(int64_t total, float* w, __nv_bfloat16* wb, const float* g, float* m1, float* m2, float lr,
                         float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
 cudaError_t launch_to_bf16(int64_t total, const float* w, __nv_bfloat16* wb, cudaStream_t s);
