@@ -226,8 +226,8 @@ def run_ours(args):
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
-    if rank == 0 and not args.no_e2e:
-        e2e = run_e2e(ens, ctx, km, stream, args)
+    if not args.no_e2e:
+        e2e = run_e2e(ens, ctx, km, stream, args, dist, dev, world)
 
     # ---- roofline of the dominant kernel ----
     if all(k is not None for k in kernel_ms_steps):
@@ -249,7 +249,9 @@ def run_ours(args):
                                     if FP64_INST_PER_KM_TRIAL else None)}
 
     secondary = {}
-    if rank == 0 and not args.quick:
+    # single-GPU secondaries: at N > 1 they would hold every rank's GPU while
+    # rank 0 alone works
+    if rank == 0 and world == 1 and not args.quick:
         secondary = run_secondary(ens, torch, stream, dev)
         secondary["km_fp32c_vs_fp64_1024x1024"] = run_config4(ens, torch, stream, dev)
         secondary["km_work_precision_16384f"] = run_work_precision(ens, torch, stream, dev)
@@ -297,9 +299,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(ens, ctx, km, stream, args):
+def run_e2e(ens, ctx, km, stream, args, dist=None, dev=None, world=1):
     """Same metric through the public API with HOST buffers: host planner,
-    host->device inputs, solve, device->host accessories and status."""
+    host->device inputs, solve, device->host accessories and status.  Every
+    rank runs its shard; a step's time is the slowest rank's (barrier on both
+    sides), its steps and copied bytes are summed over ranks."""
     import torch
     ph = km["phys"]
     n = ph["pA1"].size
@@ -313,6 +317,8 @@ def run_e2e(ens, ctx, km, stream, args):
     steps = 0.0
     for k in range(args.e2e_steps):
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         t0 = time.perf_counter()
         ens.ens_km_coefficients(*[pinned[k2] for k2 in ("pA1", "f1", "pA2", "f2", "theta", "RE")],
                                 km["liquid"], out=C_h, stream=stream)
@@ -325,8 +331,16 @@ def run_e2e(ens, ctx, km, stream, args):
         if st != ens.ENS_OK:
             raise RuntimeError(ens.ens_last_error(ctx))
         steps += float(ens.ens_read(ctx, ens.ENS_NSTEPS).sum())
+    if dist is not None:
+        t = torch.tensor(times + [steps], dtype=torch.float64, device=dev)
+        tmax, tsum = t.clone(), t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        times = [float(v) for v in tmax[:-1]]
+        steps = float(tsum[-1])
     return {"value": steps / sum(times), "unit": "system-steps/s",
-            "h2d_bytes_per_step": int((13 + 2) * n * 8), "d2h_bytes_per_step": int(rows * n * 8 + n * 4),
+            "h2d_bytes_per_step": int((13 + 2) * n * 8) * world,
+            "d2h_bytes_per_step": int(rows * n * 8 + n * 4) * world,
             "steps": args.e2e_steps, "s_per_step": sum(times) / len(times)}
 
 
