@@ -113,18 +113,22 @@ __device__ __forceinline__ double rcp_nr(double d) {
   return fma(fma(e, e, e), v, v);
 }
 
-// sqrt(x) for x >= 0 (0 for x = 0): the hardware reciprocal square root
+// sqrt(x) for x >= 0: the hardware reciprocal square root
 // approximation (PTX rsqrt.approx.ftz.f64) refined by one third-order
 // Newton-Raphson step for 1/sqrt(x), r (1 + e/2 + 3 e^2/8) with e = 1 - x r^2
 // (the binomial series of (1 - e)^(-1/2)), which cubes the seed's relative
 // error; then sqrt(x) = x r.  Within about 2 ulp, not correctly rounded;
 // 7 FP64 instructions after the seed against about 9 for sqrt().
 __device__ __forceinline__ double sqrt_nr(double x) {
+  // zero, subnormal (the seed flushes them), infinite and NaN x take the
+  // library square root; the range test is one unsigned compare on the high
+  // word (normal positive doubles have 0x00100000 <= hi < 0x7ff00000)
+  if ((unsigned)__double2hiint(x) - 0x00100000u >= 0x7fe00000u) return sqrt(x);
   double r;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
   const double e = fma(-x, r * r, 1.0);
   const double rr = fma(r * e, fma(0.375, e, 0.5), r);
-  return x > 0.0 ? x * rr : 0.0;
+  return x * rr;
 }
 
 // sin(2 pi x) and cos(2 pi x) together for |x| < 2^49.  The argument is split

@@ -82,6 +82,8 @@ def test_null_context_calls_are_harmless(ens):
     assert L.ens_solve(None, None) == ens.ENS_EINVAL
     assert L.ens_sync(None) == ens.ENS_EINVAL
     assert L.ens_acc_rows(None) == 0
+    ms = ctypes.c_double(1.0)
+    assert L.ens_kernel_ms(None, ctypes.byref(ms)) == ens.ENS_EINVAL
     L.ens_destroy(None)
 
 
