@@ -348,6 +348,16 @@ ens_status ens_mlp_screen(ens_mlp *m, int64_t n, const float *x, float *mean, fl
  * 1 when a tcgen05 launch since the last call gave up waiting for its tensor
  * cores (its outputs are then invalid), else 0. */
 ens_status ens_mlp_set_screen_impl(ens_mlp *m, int32_t impl, int32_t *wait_expired);
+/* Choose the training products (ens_mlp_forward, ens_mlp_loss_grad,
+ * ens_mlp_train): 1 (default) the tcgen05 kernels (forward, input gradients
+ * and the weight gradients of the three 128 x 128 layers with accumulators in
+ * tensor memory), 0 the mma.sync kernels.  Both take BF16 operands with FP32
+ * accumulation; the 2-wide first and last layers are FP32 in both.  If
+ * wait_expired is not NULL it receives 1 when a tcgen05 training launch gave
+ * up waiting for its tensor cores since the flag was last cleared (by each
+ * ens_mlp_loss_grad and ens_mlp_train call, which then return ENS_ECUDA),
+ * else 0. */
+ens_status ens_mlp_set_train_impl(ens_mlp *m, int32_t impl, int32_t *wait_expired);
 const char *ens_mlp_last_error(const ens_mlp *m);
 void ens_mlp_destroy(ens_mlp *m);
 

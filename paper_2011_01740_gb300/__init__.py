@@ -477,6 +477,20 @@ def ens_mlp_set_screen_impl(m: int, impl: int) -> int:
     return int(flag.value)
 
 
+def ens_mlp_set_train_impl(m: int, impl: int) -> int:
+    """Select the training kernels (1 tcgen05, 0 mma.sync); returns 1 if a
+    tcgen05 training launch gave up waiting for its tensor cores since the
+    flag was last cleared."""
+    L = _mlp_lib()
+    if not getattr(L, "_train_impl_bound", False):
+        L.ens_mlp_set_train_impl.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.ens_mlp_set_train_impl.restype = ctypes.c_int
+        L._train_impl_bound = True
+    flag = ctypes.c_int32(0)
+    _mcheck(L.ens_mlp_set_train_impl(m, int(impl), ctypes.byref(flag)), m)
+    return int(flag.value)
+
+
 def ens_mlp_last_error(m: int | None = None) -> str:
     return _mlp_lib().ens_mlp_last_error(m).decode(errors="replace")
 

@@ -33,6 +33,10 @@ struct ens_mlp {
   float* dout = nullptr;
   float* loss = nullptr;          // [members]
   float* gpart = nullptr;         // [kMaxSplits][members][kP] partial gradients of the batch slices
+  // training products: 1 tcgen05 kernels (mlp_tc05_train.cu), 0 mma.sync kernels (mlp.cu)
+  int train_impl = 1;
+  unsigned* train_err = nullptr;  // set by a tcgen05 training kernel whose wait expired
+  __nv_bfloat16* wbfT = nullptr;  // [members][3][128][128] transposed hidden weights (tcgen05 backward)
   // screening on the tcgen05 tensor cores
   int screen_impl = 1;            // 1: tcgen05 kernel, 0: mma.sync fused kernel
   float* screen_out = nullptr;    // [members][screen_cap][2]
@@ -96,6 +100,11 @@ ens_status ensure_batch(ens_mlp* m, int64_t B) {
   if (e == cudaSuccess) e = cudaMalloc(&m->dout, M * B * 2 * sizeof(float));
   if (e == cudaSuccess && !m->gpart)
     e = cudaMalloc(&m->gpart, (size_t)mlp::kMaxSplits * M * mlp::kP * sizeof(float));
+  if (e == cudaSuccess && !m->wbfT) e = cudaMalloc(&m->wbfT, M * 3 * mlp::H * mlp::H * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess && !m->train_err) {
+    e = cudaMalloc(&m->train_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(m->train_err, 0, sizeof(unsigned));
+  }
   if (e != cudaSuccess) {
     merr(m, "batch scratch: %s", cudaGetErrorString(e));
     return ENS_ENOMEM;
@@ -104,40 +113,89 @@ ens_status ensure_batch(ens_mlp* m, int64_t B) {
   return ENS_OK;
 }
 
+// arguments of the tcgen05 training kernels over the batch scratch
+mlp::TrainTcArgs tc_args(ens_mlp* m, int64_t B, const float* x, float* out, float* loss, int64_t rows) {
+  mlp::TrainTcArgs t{};
+  t.n = B;
+  t.members = m->members;
+  t.x = x;
+  t.y = m->yb;
+  t.master = m->master;
+  t.wbf = m->wbf;
+  t.wbfT = m->wbfT;
+  t.z = m->z;
+  t.out = out;
+  t.dout = m->dout;
+  t.dz = m->dz;
+  t.loss = loss;
+  t.grad = m->gpart;
+  t.rows = rows;
+  t.error = m->train_err;
+  return t;
+}
+
 // forward (training form) + backward + weight gradients of one batch already
-// in m->xb / m->yb; loss[members] accumulates the per-sample loss sum.
-ens_status batch_grad(ens_mlp* m, int64_t B, float* loss, cudaStream_t s) {
-  mlp::FwdArgs f{};
-  f.n = B;
-  f.members = m->members;
-  f.x = m->xb;
-  f.master = m->master;
-  f.wbf = m->wbf;
-  f.z = m->z;
-  f.out = m->out;
-  MLP_CUDA(m, mlp::launch_forward_train(f, s));
-  mlp::BwdArgs b{};
-  b.n = B;
-  b.y = m->yb;
-  b.master = m->master;
-  b.wbf = m->wbf;
-  b.z = m->z;
-  b.out = m->out;
-  b.dout = m->dout;
-  b.dz = m->dz;
-  b.loss = loss;
-  MLP_CUDA(m, mlp::launch_backward(b, m->members, s));
-  mlp::GradArgs g{};
-  g.n = B;
-  g.x = m->xb;
-  g.z = m->z;
-  g.dz = m->dz;
-  g.dout = m->dout;
-  g.grad = m->gpart;
+// in m->xb / m->yb; loss[members] accumulates the per-sample loss sum.  The
+// gradient is left as slice partials in m->gpart, their number in *splits;
+// with splits == nullptr they are summed into m->grad.
+ens_status batch_grad(ens_mlp* m, int64_t B, float* loss, cudaStream_t s, int* splits_out) {
   const int splits = mlp::grad_splits(B);
-  g.rows = ((B + splits - 1) / splits + mlp::kChunk - 1) / mlp::kChunk * mlp::kChunk;
-  MLP_CUDA(m, mlp::launch_wgrad(g, m->members, splits, s));
-  MLP_CUDA(m, mlp::launch_grad_reduce(m->members, splits, m->gpart, m->grad, s));
+  const int64_t rows = ((B + splits - 1) / splits + mlp::kChunk - 1) / mlp::kChunk * mlp::kChunk;
+  if (m->train_impl == 1) {
+    // tcgen05: forward, input gradients, weight gradients (the 2-wide layers
+    // 1 and 5 in FP32 by blocks of the same launch)
+    const mlp::TrainTcArgs t = tc_args(m, B, m->xb, m->out, loss, rows);
+    MLP_CUDA(m, mlp::launch_train_tc05(0, t, splits, s));
+    MLP_CUDA(m, mlp::launch_train_tc05(1, t, splits, s));
+    MLP_CUDA(m, mlp::launch_train_tc05(2, t, splits, s));
+  } else {
+    mlp::FwdArgs f{};
+    f.n = B;
+    f.members = m->members;
+    f.x = m->xb;
+    f.master = m->master;
+    f.wbf = m->wbf;
+    f.z = m->z;
+    f.out = m->out;
+    MLP_CUDA(m, mlp::launch_forward_train(f, s));
+    mlp::BwdArgs b{};
+    b.n = B;
+    b.y = m->yb;
+    b.master = m->master;
+    b.wbf = m->wbf;
+    b.z = m->z;
+    b.out = m->out;
+    b.dout = m->dout;
+    b.dz = m->dz;
+    b.loss = loss;
+    MLP_CUDA(m, mlp::launch_backward(b, m->members, s));
+    mlp::GradArgs g{};
+    g.n = B;
+    g.x = m->xb;
+    g.z = m->z;
+    g.dz = m->dz;
+    g.dout = m->dout;
+    g.grad = m->gpart;
+    g.rows = rows;
+    MLP_CUDA(m, mlp::launch_wgrad(g, m->members, splits, s));
+  }
+  if (splits_out)
+    *splits_out = splits;
+  else
+    MLP_CUDA(m, mlp::launch_grad_reduce(m->members, splits, m->gpart, m->grad, s));
+  return ENS_OK;
+}
+
+// after a synchronous call: a tcgen05 training kernel that gave up waiting
+// for its tensor cores leaves invalid results
+ens_status check_train_err(ens_mlp* m) {
+  if (m->train_impl != 1 || !m->train_err) return ENS_OK;
+  unsigned e = 0;
+  MLP_CUDA(m, cudaMemcpy(&e, m->train_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (e) {
+    merr(m, "tcgen05 training kernel: wait for the tensor cores expired");
+    return ENS_ECUDA;
+  }
   return ENS_OK;
 }
 
@@ -334,6 +392,10 @@ ens_status ens_mlp_forward(ens_mlp* m, int64_t n, const float* x, float* out, vo
   cudaStream_t s = (cudaStream_t)stream;
   ens_status st = ensure_batch(m, n);
   if (st != ENS_OK) return st;
+  if (m->train_impl == 1) {
+    MLP_CUDA(m, mlp::launch_train_tc05(0, tc_args(m, n, x, out, m->loss, n), 1, s));
+    return ENS_OK;
+  }
   mlp::FwdArgs f{};
   f.n = n;
   f.members = m->members;
@@ -359,12 +421,15 @@ ens_status ens_mlp_loss_grad(ens_mlp* m, int64_t n, const float* x, const float*
   MLP_CUDA(m, cudaMemcpyAsync(m->xb, x, n * 2 * sizeof(float), cudaMemcpyDeviceToDevice, s));
   MLP_CUDA(m, cudaMemcpyAsync(m->yb, y, n * 2 * sizeof(float), cudaMemcpyDeviceToDevice, s));
   MLP_CUDA(m, cudaMemsetAsync(m->loss, 0, m->members * sizeof(float), s));
-  st = batch_grad(m, n, m->loss, s);
+  MLP_CUDA(m, cudaMemsetAsync(m->train_err, 0, sizeof(unsigned), s));
+  st = batch_grad(m, n, m->loss, s, nullptr);
   if (st != ENS_OK) return st;
   std::vector<float> l(m->members);
   MLP_CUDA(m, cudaMemcpyAsync(l.data(), m->loss, m->members * sizeof(float), cudaMemcpyDeviceToHost, s));
   MLP_CUDA(m, cudaMemcpyAsync(grad, m->grad, (size_t)m->members * mlp::kP * sizeof(float), cudaMemcpyDefault, s));
   MLP_CUDA(m, cudaStreamSynchronize(s));
+  st = check_train_err(m);
+  if (st != ENS_OK) return st;
   for (int k = 0; k < m->members; ++k) loss[k] = l[k] / (float)n;
   return ENS_OK;
 }
@@ -392,6 +457,7 @@ ens_status ens_mlp_train(ens_mlp* m, int64_t n, const float* x, const float* y, 
     return ENS_ENOMEM;
   }
   e = cudaMemsetAsync(hist_d, 0, (size_t)std::max(1, cfg->epochs) * m->members * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->train_err, 0, sizeof(unsigned), s);
   std::vector<int32_t> perm(n);
   const int64_t tot = (int64_t)m->members * mlp::kP;
   const int64_t steps_total = (int64_t)cfg->epochs * ((n + B - 1) / B);
@@ -410,7 +476,8 @@ ens_status ens_mlp_train(ens_mlp* m, int64_t n, const float* x, const float* y, 
       const int64_t nb = std::min<int64_t>(B, n - b0);
       e = mlp::launch_gather(nb, perm_d + b0, x, y, m->xb, m->yb, s);
       if (e != cudaSuccess) break;
-      st = batch_grad(m, nb, hist_d + (size_t)ep * m->members, s);
+      int splits = 1;
+      st = batch_grad(m, nb, hist_d + (size_t)ep * m->members, s, &splits);
       if (st != ENS_OK) break;
       m->adam_t += 1;
       const float c1 = 1.0f - powf(cfg->beta1, (float)m->adam_t);
@@ -422,7 +489,7 @@ ens_status ens_mlp_train(ens_mlp* m, int64_t n, const float* x, const float* y, 
         lr = (float)(cfg->lr_final + 0.5 * (cfg->lr - cfg->lr_final) * (1.0 + cos(3.14159265358979323846 * x)));
       }
       ++step;
-      e = mlp::launch_adam(tot, m->master, m->wbf, m->grad, m->m1, m->m2, lr, cfg->beta1, cfg->beta2,
+      e = mlp::launch_adam(tot, m->master, m->wbf, m->gpart, splits, m->m1, m->m2, lr, cfg->beta1, cfg->beta2,
                            cfg->eps, c1, c2, s);
     }
     if (st != ENS_OK) break;
@@ -444,7 +511,7 @@ ens_status ens_mlp_train(ens_mlp* m, int64_t n, const float* x, const float* y, 
     merr(m, "training: %s", cudaGetErrorString(e));
     return ENS_ECUDA;
   }
-  return ENS_OK;
+  return check_train_err(m);
 }
 
 ens_status ens_mlp_screen(ens_mlp* m, int64_t n, const float* x, float* mean, float* stdv, float* p1,
@@ -499,6 +566,17 @@ ens_status ens_mlp_set_screen_impl(ens_mlp* m, int32_t impl, int32_t* wait_expir
   return ENS_OK;
 }
 
+ens_status ens_mlp_set_train_impl(ens_mlp* m, int32_t impl, int32_t* wait_expired) {
+  if (!m || (impl != 0 && impl != 1)) return ENS_EINVAL;
+  if (wait_expired) {
+    unsigned e = 0;
+    if (m->train_err) MLP_CUDA(m, cudaMemcpy(&e, m->train_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    *wait_expired = (int32_t)e;
+  }
+  m->train_impl = impl;
+  return ENS_OK;
+}
+
 const char* ens_mlp_last_error(const ens_mlp* m) { return m ? m->err : g_mlp_err; }
 
 void ens_mlp_destroy(ens_mlp* m) {
@@ -518,6 +596,8 @@ void ens_mlp_destroy(ens_mlp* m) {
   cudaFree(m->dout);
   cudaFree(m->screen_out);
   cudaFree(m->screen_err);
+  cudaFree(m->train_err);
+  cudaFree(m->wbfT);
   delete m;
 }
 

@@ -24,11 +24,6 @@ namespace mlp {
 __host__ __device__ constexpr int64_t w_off(int l) { return l == 1 ? oW1 : l == 2 ? oW2 : l == 3 ? oW3 : l == 4 ? oW4 : oW5; }
 __host__ __device__ constexpr int64_t b_off(int l) { return l == 1 ? ob1 : l == 2 ? ob2 : l == 3 ? ob3 : l == 4 ? ob4 : ob5; }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
-}
-
 // D += A * B for one m16n8k16 tile (BF16 inputs, FP32 accumulate).
 __device__ __forceinline__ void mma16816(float* c, const uint32_t* a, const uint32_t* b) {
   asm volatile(
@@ -153,27 +148,27 @@ __global__ void __launch_bounds__(kThreads) mlp_forward_kernel(FwdArgs a) {
   float* outs = reinterpret_cast<float*>(Ws + H * LDA);  // [members][kTile][2]
   const int64_t row0 = (int64_t)blockIdx.x * kTile;
   const int rows = (int)((a.n - row0) < kTile ? (a.n - row0) : kTile);
-  if (TRAIN) {
+  if constexpr (TRAIN) {
     tile_forward(a, blockIdx.y, row0, rows, act0, act1, Ws, outs, true);
-    return;
-  }
-  for (int m = 0; m < a.members; ++m) tile_forward(a, m, row0, rows, act0, act1, Ws, outs + m * kTile * 2, false);
-  const int r = threadIdx.x;
-  if (r < rows) {
-    float s = 0.f, s2 = 0.f, p = 0.f;
-    for (int m = 0; m < a.members; ++m) {
-      const float o = outs[m * kTile * 2 + r * 2];
-      s += o;
-      p += 1.0f / (1.0f + __expf(-outs[m * kTile * 2 + r * 2 + 1]));
+  } else {
+    for (int m = 0; m < a.members; ++m) tile_forward(a, m, row0, rows, act0, act1, Ws, outs + m * kTile * 2, false);
+    const int r = threadIdx.x;
+    if (r < rows) {
+      float s = 0.f, s2 = 0.f, p = 0.f;
+      for (int m = 0; m < a.members; ++m) {
+        const float o = outs[m * kTile * 2 + r * 2];
+        s += o;
+        p += 1.0f / (1.0f + __expf(-outs[m * kTile * 2 + r * 2 + 1]));
+      }
+      const float mu = s / a.members;
+      for (int m = 0; m < a.members; ++m) {
+        const float d = outs[m * kTile * 2 + r * 2] - mu;
+        s2 += d * d;
+      }
+      a.mean[row0 + r] = mu;
+      a.stdv[row0 + r] = sqrtf(s2 / a.members);
+      a.p1[row0 + r] = p / a.members;
     }
-    const float mu = s / a.members;
-    for (int m = 0; m < a.members; ++m) {
-      const float d = outs[m * kTile * 2 + r * 2] - mu;
-      s2 += d * d;
-    }
-    a.mean[row0 + r] = mu;
-    a.stdv[row0 + r] = sqrtf(s2 / a.members);
-    a.p1[row0 + r] = p / a.members;
   }
 }
 
@@ -186,7 +181,6 @@ __global__ void __launch_bounds__(kThreads) mlp_backward_kernel(BwdArgs a) {
   float* dsh = reinterpret_cast<float*>(Ws + H * LDA);           // [kTile][2] dout
   __shared__ float red[kThreads / 32];
   const int m = blockIdx.y;
-  const float* P = a.master + (int64_t)m * kP;
   const __nv_bfloat16* Pb = a.wbf + (int64_t)m * kPS;
   const int64_t row0 = (int64_t)blockIdx.x * kTile;
   const int rows = (int)((a.n - row0) < kTile ? (a.n - row0) : kTile);
@@ -264,7 +258,6 @@ __global__ void __launch_bounds__(kThreads) mlp_backward_kernel(BwdArgs a) {
       }
     }
   }
-  (void)P;
 }
 
 
@@ -283,48 +276,7 @@ __global__ void __launch_bounds__(kThreads) mlp_wgrad_kernel(GradArgs a) {
   const int64_t r0 = (int64_t)blockIdx.z * a.rows;
   const int64_t r1 = r0 + a.rows < a.n ? r0 + a.rows : a.n;
   if (l == 1 || l == 5) {
-    // thread = (feature f, half of the slice)
-    const int f = tid & (H - 1), half = tid >> 7;
-    const int64_t mid = r0 + (r1 - r0) / 2;
-    const int64_t b0 = half ? mid : r0, b1 = half ? r1 : mid;
-    float s0 = 0.f, s1 = 0.f, sb = 0.f;
-    if (l == 1) {
-      for (int64_t b = b0; b < b1; ++b) {
-        const float d = a.dz[(((int64_t)m * 4 + 0) * a.n + b) * H + f];
-        s0 = fmaf(d, a.x[2 * b], s0);
-        s1 = fmaf(d, a.x[2 * b + 1], s1);
-        sb += d;
-      }
-    } else {
-      for (int64_t b = b0; b < b1; ++b) {
-        const float h = gelu(a.z[(((int64_t)m * a.n + b) * 4 + 3) * H + f]);
-        s0 = fmaf(a.dout[((int64_t)m * a.n + b) * 2], h, s0);
-        s1 = fmaf(a.dout[((int64_t)m * a.n + b) * 2 + 1], h, s1);
-      }
-      if (f == 0) {
-        for (int64_t b = b0; b < b1; ++b) sb += a.dout[((int64_t)m * a.n + b) * 2];
-      } else if (f == 1) {
-        for (int64_t b = b0; b < b1; ++b) sb += a.dout[((int64_t)m * a.n + b) * 2 + 1];
-      }
-    }
-    part[tid * 3 + 0] = s0;
-    part[tid * 3 + 1] = s1;
-    part[tid * 3 + 2] = sb;
-    __syncthreads();
-    if (tid < H) {
-      const float w0 = part[tid * 3] + part[(tid + H) * 3];
-      const float w1 = part[tid * 3 + 1] + part[(tid + H) * 3 + 1];
-      const float bb = part[tid * 3 + 2] + part[(tid + H) * 3 + 2];
-      if (l == 1) {
-        G[oW1 + 2 * tid] = w0;
-        G[oW1 + 2 * tid + 1] = w1;
-        G[ob1 + tid] = bb;
-      } else {
-        G[oW5 + tid] = w0;
-        G[oW5 + H + tid] = w1;
-        if (tid < 2) G[ob5 + tid] = bb;
-      }
-    }
+    wgrad_fp32_layer(l, m, a.n, r0, r1, a.x, a.z, a.dz, a.dout, G, part);
     return;
   }
   // tensor-core layers: As[out][k] = dz_l[b][out], Bs[in][k] = gelu(z_{l-1}[b][in])
@@ -369,10 +321,13 @@ __global__ void __launch_bounds__(kThreads) mlp_wgrad_kernel(GradArgs a) {
 
 
 // Adam (Kingma & Ba 2015) on the FP32 master weights; refreshes the BF16 copy.
-__global__ void adam_kernel(int64_t total, float* w, __nv_bfloat16* wb, const float* g, float* m1, float* m2,
-                            float lr, float b1, float b2, float eps, float c1, float c2) {
+// Adam step; the gradient is the sum of the slice partials part[k][i], k in
+// order (the same sums as mlp_grad_reduce_kernel)
+__global__ void adam_kernel(int64_t total, float* w, __nv_bfloat16* wb, const float* part, int splits, float* m1,
+                            float* m2, float lr, float b1, float b2, float eps, float c1, float c2) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
+    float gi = part[i];
+    for (int k = 1; k < splits; ++k) gi += part[(int64_t)k * total + i];
     const float a = fmaf(b1, m1[i], (1.0f - b1) * gi);
     const float v = fmaf(b2, m2[i], (1.0f - b2) * gi * gi);
     m1[i] = a;
@@ -475,9 +430,9 @@ cudaError_t launch_grad_reduce(int members, int splits, const float* part, float
   return cudaGetLastError();
 }
 
-cudaError_t launch_adam(int64_t total, float* w, __nv_bfloat16* wb, const float* g, float* m1, float* m2, float lr,
-                        float b1, float b2, float eps, float c1, float c2, cudaStream_t s) {
-  adam_kernel<<<grid_1d(total), 256, 0, s>>>(total, w, wb, g, m1, m2, lr, b1, b2, eps, c1, c2);
+cudaError_t launch_adam(int64_t total, float* w, __nv_bfloat16* wb, const float* part, int splits, float* m1,
+                        float* m2, float lr, float b1, float b2, float eps, float c1, float c2, cudaStream_t s) {
+  adam_kernel<<<grid_1d(total), 256, 0, s>>>(total, w, wb, part, splits, m1, m2, lr, b1, b2, eps, c1, c2);
   return cudaGetLastError();
 }
 

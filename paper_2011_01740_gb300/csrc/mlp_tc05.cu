@@ -27,15 +27,15 @@
 #include <cstdint>
 
 #include "mlp.cuh"
+#include "tc05.cuh"
 
 namespace ens {
 namespace mlp {
 
 namespace {
 
-constexpr int kTcThreads = 128;
-constexpr uint32_t kTmemCols = 128;
-constexpr size_t kMatBytes = (size_t)H * H * sizeof(__nv_bfloat16);  // 32 KB
+using namespace tc05;
+constexpr int kTcThreads = tc05::kThreads;
 // shared memory map (bytes from the 1024-aligned base)
 constexpr size_t kSW = 0;                      // W2, W3, W4 (3 x 32 KB)
 constexpr size_t kSA = kSW + 3 * kMatBytes;    // activation tile (32 KB)
@@ -43,76 +43,6 @@ constexpr size_t kSF = kSA + kMatBytes;        // fp32 W1[256], b1..b4[4][128], 
 constexpr size_t kSFFloats = 256 + 4 * 128 + 256 + 2;
 constexpr size_t kSBar = kSF + ((kSFFloats * 4 + 15) / 16) * 16;   // mbarrier (8 B) + TMEM slot (4 B)
 constexpr size_t kTcSmem = kSBar + 64 + 1024;  // + alignment slack
-constexpr uint32_t kWaitLimit = 1u << 20;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// byte offset of element (r, k) of a 128 x 128 BF16 operand in core-matrix layout
-__device__ __forceinline__ uint32_t core_off(int r, int k) {
-  return (uint32_t)(((r >> 3) * 16 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-// shared-memory matrix descriptor: start >> 4, LBO = 128 B, SBO = 2048 B,
-// descriptor version 1 (bit 46), no swizzle
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)(128u >> 4) << 16;
-  d |= (uint64_t)(2048u >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
-// N = 128 (bits 17-22 = N >> 3), M = 128 (bits 24-28 = M >> 4)
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// bounded wait for the mbarrier phase `parity`; returns false on expiry
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 
 }  // namespace
 
@@ -195,7 +125,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_screen_tc05_kernel(TcArgs a
         const int f = kc * 8 + 2 * j;
         const float z0 = fmaf(sW1[2 * f + 1], x1, fmaf(sW1[2 * f], x0, sB[f]));
         const float z1 = fmaf(sW1[2 * f + 3], x1, fmaf(sW1[2 * f + 2], x0, sB[f + 1]));
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_f(z0), gelu_f(z1));
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu(z0), gelu(z1));
         pk[j] = *reinterpret_cast<uint32_t*>(&h2);
       }
       *reinterpret_cast<uint4*>(smem + kSA + core_off(tid, kc * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -231,8 +161,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_screen_tc05_kernel(TcArgs a
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               const int col = c * 32 + q * 8 + 2 * j;
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_f(v[q * 8 + 2 * j] + bl[col]),
-                                                        gelu_f(v[q * 8 + 2 * j + 1] + bl[col + 1]));
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu(v[q * 8 + 2 * j] + bl[col]),
+                                                        gelu(v[q * 8 + 2 * j + 1] + bl[col + 1]));
               pk[j] = *reinterpret_cast<uint32_t*>(&h2);
             }
             *reinterpret_cast<uint4*>(smem + kSA + core_off(tid, c * 32 + q * 8)) =
@@ -243,7 +173,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_screen_tc05_kernel(TcArgs a
           for (int j = 0; j < 32; ++j) {
             const int col = c * 32 + j;
             // round to BF16 like the activations of the hidden layers
-            const float h = __bfloat162float(__float2bfloat16(gelu_f(v[j] + bl[col])));
+            const float h = __bfloat162float(__float2bfloat16(gelu(v[j] + bl[col])));
             o0 = fmaf(h, sW5[col], o0);
             o1 = fmaf(h, sW5[128 + col], o1);
           }

@@ -25,10 +25,23 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _model(members, params):
+def _model(members, params, train_impl=1):
     m = ens.ens_mlp_create(members, W.SEED)
     ens.ens_mlp_set_params(m, params)
+    ens.ens_mlp_set_train_impl(m, train_impl)
     return m
+
+
+def _loss_grad(p, x, y, impl):
+    M, n = p.shape[0], x.shape[0]
+    m = _model(M, p, impl)
+    try:
+        grad = np.empty((M, W.MLP_PARAMS), dtype=np.float32)
+        loss = ens.ens_mlp_loss_grad(m, n, _dev(x), _dev(y), M, grad)
+        assert ens.ens_mlp_set_train_impl(m, impl) == 0            # no expired tensor-core wait
+    finally:
+        ens.ens_mlp_destroy(m)
+    return loss, grad
 
 
 def _blocks():
@@ -53,13 +66,15 @@ def test_params_round_trip():
         ens.ens_mlp_destroy(m)
 
 
+@pytest.mark.parametrize("impl", [1, 0])
 @pytest.mark.parametrize("n", [1, 77, 128, 1000])
-def test_forward_matches_oracle(n):
+def test_forward_matches_oracle(n, impl):
+    """Training-form forward (impl 1: tcgen05, 0: mma.sync)."""
     import torch
     M = 4
     p = W.mlp_params(M)
     x, _ = W.mlp_batch(n)
-    m = _model(M, p)
+    m = _model(M, p, impl)
     try:
         out = torch.empty((M, n, 2), dtype=torch.float32, device="cuda")
         ens.ens_mlp_forward(m, n, _dev(x), out)
@@ -73,19 +88,16 @@ def test_forward_matches_oracle(n):
         assert err < BF16_TOL, (k, err)
 
 
-def test_gradient_matches_oracle():
-    """Loss and gradient of one batch of 300 samples (3 tiles with a ragged
-    tail) for every member and every parameter block."""
-    import torch
-    M, n = 4, 300
+@pytest.mark.parametrize("impl", [1, 0])
+@pytest.mark.parametrize("n", [300, 5000])
+def test_gradient_matches_oracle(n, impl):
+    """Loss and gradient of one batch for every member and every parameter
+    block: 300 samples (3 tiles with a ragged tail, 3 weight-gradient slices)
+    and 5,000 (8 slices of 640 samples, 5 chunks each, the last one ragged)."""
+    M = 4
     p = W.mlp_params(M)
     x, y = W.mlp_batch(n)
-    m = _model(M, p)
-    try:
-        grad = np.empty((M, W.MLP_PARAMS), dtype=np.float32)
-        loss = ens.ens_mlp_loss_grad(m, n, _dev(x), _dev(y), M, grad)
-    finally:
-        ens.ens_mlp_destroy(m)
+    loss, grad = _loss_grad(p, x, y, impl)
     for k in range(M):
         L, g = omlp.grad(p[k].astype(np.float64), x.astype(np.float64), y.astype(np.float64))
         assert abs(loss[k] - L) < BF16_TOL * abs(L), (k, loss[k], L)
@@ -151,12 +163,31 @@ def test_screen_tcgen05_large_grid_matches_mma_sync():
         np.testing.assert_allclose(a, b, rtol=2e-2, atol=2e-2)
 
 
-def test_training_reduces_loss():
+def test_tcgen05_gradient_agrees_with_mma_sync():
+    """The two training implementations round the same operands to BF16 and
+    accumulate in FP32; they differ only in the order of the FP32 sums, so
+    their gradients agree far inside the tolerance against the oracle."""
+    M, n = 3, 2000
+    p = W.mlp_params(M, seed=6)
+    x, y = W.mlp_batch(n, seed=8)
+    l1, g1 = _loss_grad(p, x, y, 1)
+    l0, g0 = _loss_grad(p, x, y, 0)
+    np.testing.assert_allclose(l1, l0, rtol=1e-5)
+    for k in range(M):
+        for name, lo, hi in _blocks():
+            err = np.linalg.norm(g1[k, lo:hi] - g0[k, lo:hi]) / max(np.linalg.norm(g0[k, lo:hi]), 1e-30)
+            assert err < 2e-3, (k, name, err)
+
+
+@pytest.mark.parametrize("impl", [1, 0])
+def test_training_reduces_loss(impl):
     M, n = 4, 8192
     x, y = W.mlp_batch(n, seed=11)
     m = ens.ens_mlp_create(M, W.SEED)
+    ens.ens_mlp_set_train_impl(m, impl)
     try:
         hist = ens.ens_mlp_train(m, n, _dev(x), _dev(y), ens.make_train_cfg(epochs=40, batch=512, lr=2e-3), M)
+        assert ens.ens_mlp_set_train_impl(m, impl) == 0
     finally:
         ens.ens_mlp_destroy(m)
     assert hist.shape == (40, M)
