@@ -719,6 +719,20 @@ def run_profile_case(case: str):
         print(json.dumps({"case": case, "points": n, "members": 4,
                           "mac_per_point_member": 49664}), flush=True)
         return
+    elif case == "mlp_train":
+        # two epochs over 8,192 samples, batch 1024 (8 Adam steps per epoch):
+        # the second epoch's launches are the ones to capture
+        import torch
+        x, y = W.mlp_batch(8192, seed=11)
+        m = ens.ens_mlp_create(4, W.SEED)
+        hist = ens.ens_mlp_train(m, 8192, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(),
+                                 ens.make_train_cfg(epochs=2, batch=1024, lr=2e-3), 4)
+        torch.cuda.synchronize()
+        ens.ens_mlp_destroy(m)
+        print(json.dumps({"case": case, "samples": 8192, "batch": 1024, "members": 4, "epochs": 2,
+                          "flop_per_launch_per_kernel": 3 * 2 * 128 * 128 * 1024 * 4,
+                          "loss": [float(hist[0].mean()), float(hist[-1].mean())]}), flush=True)
+        return
     elif case == "prv":
         wl = W.prv(8192, t1=64.0)
         t = wl["tol"]
@@ -747,7 +761,9 @@ def run_profile_case(case: str):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", default=None, help="run one small case for ncu (km, prv, x2p, lorenz)")
+    ap.add_argument("--profile", default=None,
+                    help="run one small case for ncu (km, km_full64, km_full2, km_fp32c, mlp_screen, mlp_train, "
+                         "prv, x2p, lorenz)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)

@@ -28,6 +28,7 @@ struct ens_mlp {
   float* xb = nullptr;
   float* yb = nullptr;
   float* z = nullptr;
+  float* gp = nullptr;            // gelu'(z) of the tcgen05 forward, [members][B][4][128]
   float* dz = nullptr;
   float* out = nullptr;
   float* dout = nullptr;
@@ -86,15 +87,17 @@ ens_status ensure_batch(ens_mlp* m, int64_t B) {
   cudaFree(m->xb);
   cudaFree(m->yb);
   cudaFree(m->z);
+  cudaFree(m->gp);
   cudaFree(m->dz);
   cudaFree(m->out);
   cudaFree(m->dout);
-  m->xb = m->yb = m->z = m->dz = m->out = m->dout = nullptr;
+  m->xb = m->yb = m->z = m->gp = m->dz = m->out = m->dout = nullptr;
   m->cap = 0;
   const size_t M = (size_t)m->members;
   cudaError_t e = cudaMalloc(&m->xb, B * 2 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->yb, B * 2 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->z, M * B * 4 * mlp::H * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->gp, M * B * 4 * mlp::H * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->dz, M * 4 * B * mlp::H * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->out, M * B * 2 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->dout, M * B * 2 * sizeof(float));
@@ -124,6 +127,7 @@ mlp::TrainTcArgs tc_args(ens_mlp* m, int64_t B, const float* x, float* out, floa
   t.wbf = m->wbf;
   t.wbfT = m->wbfT;
   t.z = m->z;
+  t.gp = m->gp;
   t.out = out;
   t.dout = m->dout;
   t.dz = m->dz;
@@ -591,6 +595,7 @@ void ens_mlp_destroy(ens_mlp* m) {
   cudaFree(m->xb);
   cudaFree(m->yb);
   cudaFree(m->z);
+  cudaFree(m->gp);
   cudaFree(m->dz);
   cudaFree(m->out);
   cudaFree(m->dout);

@@ -70,10 +70,17 @@ struct GradArgs {
   int64_t rows;       // samples per slice (a multiple of kChunk)
 };
 
-// GELU, erf form, and its derivative
+// GELU, erf form, and its derivative: gelu(z) = z Phi(z), gelu'(z) = Phi(z) +
+// z phi(z), with Phi and phi the standard normal distribution and density
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+}
+// both from one erf evaluation (the same expressions as gelu and gelu_grad)
+__device__ __forceinline__ void gelu_and_grad(float z, float& h, float& g) {
+  const float phi2 = 1.0f + erff(z * 0.70710678118654752f);
+  h = 0.5f * z * phi2;
+  g = 0.5f * phi2 + z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
 
 // Weight and bias gradients of one 2-wide FP32 layer of member m over the
@@ -159,6 +166,7 @@ struct TrainTcArgs {
   const __nv_bfloat16* wbf;  // [members][kPS]
   __nv_bfloat16* wbfT;       // [members][3][128][128] W_2..W_4 transposed (written by step 1)
   float* z;                  // [members][n][4][128] pre-activations
+  float* gp;                 // [members][n][4][128] gelu'(z), written by the forward for the backward
   float* out;                // [members][n][2]
   float* dout;               // [members][n][2]
   float* dz;                 // [members][4][n][128]

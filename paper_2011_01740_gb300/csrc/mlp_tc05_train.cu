@@ -94,10 +94,9 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t bar, uint32_
   }
 }
 
-// one 128 x 128 x 128 product into TMEM and the wait for it; returns false
-// (block-uniformly) when the wait expired
-__device__ __forceinline__ bool tc_product(uint32_t tmem, uint32_t sa, uint32_t sb, bool acc, uint32_t bar,
-                                           uint32_t& parity, unsigned* error) {
+// issue one 128 x 128 x 128 product into TMEM (all threads call: the
+// operands written by every thread are fenced and published first)
+__device__ __forceinline__ void tc_issue(uint32_t tmem, uint32_t sa, uint32_t sb, bool acc, uint32_t bar) {
   fence_to_mma();
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -105,6 +104,11 @@ __device__ __forceinline__ bool tc_product(uint32_t tmem, uint32_t sa, uint32_t 
     mma_128(tmem, sa, sb, acc);
     mma_commit(bar);
   }
+}
+
+// wait for the product issued last; returns false (block-uniformly) when the
+// wait expired
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t& parity, unsigned* error) {
   const bool ok = bar_wait(bar, parity);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) atomicOr(error, 1u);
@@ -113,6 +117,12 @@ __device__ __forceinline__ bool tc_product(uint32_t tmem, uint32_t sa, uint32_t 
   parity ^= 1u;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   return true;
+}
+
+__device__ __forceinline__ bool tc_product(uint32_t tmem, uint32_t sa, uint32_t sb, bool acc, uint32_t bar,
+                                           uint32_t& parity, unsigned* error) {
+  tc_issue(tmem, sa, sb, acc, bar);
+  return tc_wait(bar, parity, error);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -135,25 +145,52 @@ __device__ __forceinline__ void load8(const float* src, bool live, float* v) {
   v[0] = lo.x, v[1] = lo.y, v[2] = lo.z, v[3] = lo.w, v[4] = hi.x, v[5] = hi.y, v[6] = hi.z, v[7] = hi.w;
 }
 
-// Stage a row-major 128 x 128 BF16 matrix M[n][k] as a K-major operand.
-// Thread index bits: 0-2 the row within a core matrix, 3-6 the 16-byte chunk
-// of the row, 7 and up the row group; a phase of 8 threads then writes one
-// whole 128-byte core matrix (no bank conflict) and a warp reads 8 rows x 64
-// contiguous bytes.  All loads are issued before the stores.
-__device__ __forceinline__ void stage_kmajor(unsigned char* dst, const __nv_bfloat16* M) {
-  constexpr int kIt = H * (H / 8) / kT;   // 8
-  uint4 v[kIt];
+// eight consecutive floats to a 16-byte aligned address
+__device__ __forceinline__ void store8(float* dst, const float* v) {
+  reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// output gradients D[b][f] and pre-activations Z[b * 512 + f] of the samples
+// b0 .. b0 + 7 (0 past r1)
+__device__ __forceinline__ void load_group(const float* D, const float* Z, int64_t b0, int64_t r1, int f, float* d,
+                                           float* z) {
 #pragma unroll
-  for (int it = 0; it < kIt; ++it) {
-    const int idx = it * kT + (int)threadIdx.x;
-    const int n = (idx >> 7) * 8 + (idx & 7), kc = (idx >> 3) & 15;
-    v[it] = *reinterpret_cast<const uint4*>(M + n * H + kc * 8);
+  for (int j = 0; j < 8; ++j) {
+    const int64_t smp = b0 + j;
+    d[j] = smp < r1 ? D[smp * H + f] : 0.f;
+    z[j] = smp < r1 ? Z[smp * 4 * H + f] : 0.f;
+  }
+}
+
+// Stage three row-major 128 x 128 BF16 matrices M_i[n][k] as K-major
+// operands at dst + i * kMatBytes.  Thread index bits: 0-2 the row within a
+// core matrix, 3-6 the 16-byte chunk of the row, 7 and up the row group; a
+// phase of 8 threads then writes one whole 128-byte core matrix (no bank
+// conflict) and a warp reads 8 rows x 64 contiguous bytes.  All 24 loads of
+// a thread are issued before its stores.
+__device__ __forceinline__ void stage3_kmajor(unsigned char* dst, const __nv_bfloat16* M0, const __nv_bfloat16* M1,
+                                              const __nv_bfloat16* M2) {
+  constexpr int kIt = H * (H / 8) / kT;   // 8 chunks per thread and matrix
+  const __nv_bfloat16* Ms[3] = {M0, M1, M2};
+  uint4 v[3][kIt];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int idx = it * kT + (int)threadIdx.x;
+      const int n = (idx >> 7) * 8 + (idx & 7), kc = (idx >> 3) & 15;
+      v[i][it] = *reinterpret_cast<const uint4*>(Ms[i] + n * H + kc * 8);
+    }
   }
 #pragma unroll
-  for (int it = 0; it < kIt; ++it) {
-    const int idx = it * kT + (int)threadIdx.x;
-    const int n = (idx >> 7) * 8 + (idx & 7), kc = (idx >> 3) & 15;
-    *reinterpret_cast<uint4*>(dst + core_off(n, kc * 8)) = v[it];
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int idx = it * kT + (int)threadIdx.x;
+      const int n = (idx >> 7) * 8 + (idx & 7), kc = (idx >> 3) & 15;
+      *reinterpret_cast<uint4*>(dst + i * kMatBytes + core_off(n, kc * 8)) = v[i][it];
+    }
   }
 }
 
@@ -191,6 +228,8 @@ __global__ void __launch_bounds__(256) mlp_transpose_w_kernel(const __nv_bfloat1
 }
 
 // Forward of one 128-sample tile of one member: grid = (tiles, members).
+// Stores the pre-activations z (for the weight gradients) and gelu'(z) (for
+// the backward) of the four hidden layers, and the outputs.
 // Sample s = tid % 128 is TMEM lane s; warpgroup hf = tid / 128 takes the
 // features 64 hf .. + 63 of every layer.
 __global__ void __launch_bounds__(kT, 1) mlp_forward_train_tc05_kernel(TrainTcArgs a) {
@@ -218,27 +257,29 @@ __global__ void __launch_bounds__(kT, 1) mlp_forward_train_tc05_kernel(TrainTcAr
   for (int i = tid; i < 512; i += kT) sB[i] = P[ob1 + (i >> 7) * (ob2 - ob1) + (i & 127)];
   if (tid < 2) sB5[tid] = P[ob5 + tid];
   // W_l [out][in] is the K-major B operand as stored
-  for (int l = 2; l <= 4; ++l) stage_kmajor(smem + kFW + (l - 2) * kMatBytes, Pb + w_of(l));
+  stage3_kmajor(smem + kFW, Pb + w_of(2), Pb + w_of(3), Pb + w_of(4));
   const uint32_t tmem = tc_setup(bar_a, tslot);   // its barrier also publishes sf
   const uint32_t sA = smem_u32(smem + kFA), sW = smem_u32(smem + kFW);
   uint32_t parity = 0;
   bool failed = false;
-  float* zrow = a.z + ((int64_t)m * a.n + (live ? p : 0)) * 4 * H;   // [4][128] of this sample
+  const int64_t row = ((int64_t)m * a.n + (live ? p : 0)) * 4 * H;   // [4][128] of this sample
+  float* zrow = a.z + row;
+  float* grow = a.gp + row;
   // layer 1 in FP32
   {
     const float x0 = live ? a.x[2 * p] : 0.f, x1 = live ? a.x[2 * p + 1] : 0.f;
     for (int kc = hf * 8; kc < hf * 8 + 8; ++kc) {
-      float zv[8], hv[8];
+      float zv[8], hv[8], gv[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int f = kc * 8 + j;
         zv[j] = fmaf(sW1[2 * f + 1], x1, fmaf(sW1[2 * f], x0, sB[f]));
-        hv[j] = gelu(zv[j]);
+        gelu_and_grad(zv[j], hv[j], gv[j]);
       }
       store_bf16x8(smem + kFA, s, kc * 8, hv);
       if (live) {
-        reinterpret_cast<float4*>(zrow)[kc * 2] = make_float4(zv[0], zv[1], zv[2], zv[3]);
-        reinterpret_cast<float4*>(zrow)[kc * 2 + 1] = make_float4(zv[4], zv[5], zv[6], zv[7]);
+        store8(zrow + kc * 8, zv);
+        store8(grow + kc * 8, gv);
       }
     }
   }
@@ -254,27 +295,26 @@ __global__ void __launch_bounds__(kT, 1) mlp_forward_train_tc05_kernel(TrainTcAr
       tmem_ld32(tmem_at(tmem, c), v);
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] += bl[c * 32 + j];
-      if (live) {
-        float4* zd = reinterpret_cast<float4*>(zrow + (l - 1) * H + c * 32);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) zd[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      }
-      if (l < 4) {
+      for (int q = 0; q < 4; ++q) {
+        const int col0 = c * 32 + q * 8;
+        float hv[8], gv[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float hv[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) hv[j] = gelu(v[q * 8 + j]);
-          store_bf16x8(smem + kFA, s, c * 32 + q * 8, hv);
+        for (int j = 0; j < 8; ++j) gelu_and_grad(v[q * 8 + j], hv[j], gv[j]);
+        if (live) {
+          store8(zrow + (l - 1) * H + col0, v + q * 8);
+          store8(grow + (l - 1) * H + col0, gv);
         }
-      } else {
+        if (l < 4) {
+          store_bf16x8(smem + kFA, s, col0, hv);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = c * 32 + j;
-          // the output layer reads the BF16-rounded activations, as the MMAs do
-          const float h = __bfloat162float(__float2bfloat16(gelu(v[j])));
-          o0 = fmaf(h, sW5[col], o0);
-          o1 = fmaf(h, sW5[128 + col], o1);
+          for (int j = 0; j < 8; ++j) {
+            // the output layer reads the BF16-rounded activations, as the MMAs do
+            const float h = __bfloat162float(__float2bfloat16(hv[j]));
+            o0 = fmaf(h, sW5[col0 + j], o0);
+            o1 = fmaf(h, sW5[128 + col0 + j], o1);
+          }
         }
       }
     }
@@ -294,6 +334,7 @@ __global__ void __launch_bounds__(kT, 1) mlp_forward_train_tc05_kernel(TrainTcAr
 // Loss, output gradient and the gradients of the pre-activations of one
 // 128-sample tile of one member: grid = (tiles, members).  dz_4 = (dout W5)
 // * gelu'(z_4) in FP32; dz_{l-1} = (dz_l W_l) * gelu'(z_{l-1}) for l = 4, 3, 2
+// (gelu'(z) as the forward wrote it)
 // on the tensor cores with W_l^T (a.wbfT) as the B operand.  Warpgroup hf
 // takes features 64 hf .. + 63; the first one also owns loss and dout.
 __global__ void __launch_bounds__(kT, 1) mlp_backward_tc05_kernel(TrainTcArgs a) {
@@ -312,14 +353,14 @@ __global__ void __launch_bounds__(kT, 1) mlp_backward_tc05_kernel(TrainTcArgs a)
   const __nv_bfloat16* Pb = a.wbf + (int64_t)m * kPS;
   for (int i = tid; i < 256; i += kT) sW5[i] = __bfloat162float(Pb[oW5 + i]);
   // B operand of the input gradient: element (n = in, k = out) = W_l^T[in][out]
-  for (int l = 2; l <= 4; ++l)
-    stage_kmajor(smem + kFW + (l - 2) * kMatBytes, a.wbfT + ((int64_t)m * 3 + (l - 2)) * H * H);
+  const __nv_bfloat16* WT = a.wbfT + (int64_t)m * 3 * H * H;
+  stage3_kmajor(smem + kFW, WT, WT + H * H, WT + 2 * H * H);
   const uint32_t tmem = tc_setup(bar_a, tslot);
   const uint32_t sA = smem_u32(smem + kFA), sW = smem_u32(smem + kFW);
   uint32_t parity = 0;
   bool failed = false;
   const float inv_n = 1.0f / (float)a.n;
-  const float* zrow = a.z + ((int64_t)m * a.n + (live ? p : 0)) * 4 * H;
+  const float* grow = a.gp + ((int64_t)m * a.n + (live ? p : 0)) * 4 * H;   // gelu'(z) of this sample
   // loss and output gradient of sample s (both warpgroups need dout)
   float d0 = 0.f, d1 = 0.f, lsum = 0.f;
   if (live) {
@@ -336,14 +377,19 @@ __global__ void __launch_bounds__(kT, 1) mlp_backward_tc05_kernel(TrainTcArgs a)
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
   if (lane == 0) red[warp] = lsum;
-  // dz_4 in FP32
-  for (int kc = hf * 8; kc < hf * 8 + 8; ++kc) {
-    float dv[8], zz[8];
-    load8(zrow + 3 * H + kc * 8, live, zz);
+  // dz_4 in FP32; gelu'(z_4) of this thread's 64 features is loaded first
+  // (16 independent 16-byte loads)
+  float gz[64];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) load8(grow + 3 * H + hf * 64 + q * 8, live, gz + q * 8);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int kc = hf * 8 + q;
+    float dv[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int f = kc * 8 + j;
-      dv[j] = live ? fmaf(d0, sW5[f], d1 * sW5[128 + f]) * gelu_grad(zz[j]) : 0.f;
+      dv[j] = live ? fmaf(d0, sW5[f], d1 * sW5[128 + f]) * gz[q * 8 + j] : 0.f;
     }
     store_bf16x8(smem + kFA, s, kc * 8, dv);
     if (live) {
@@ -359,17 +405,21 @@ __global__ void __launch_bounds__(kT, 1) mlp_backward_tc05_kernel(TrainTcArgs a)
     atomicAdd(&a.loss[m], t);
   }
   for (int l = 4; l >= 2 && !failed; --l) {
-    if (!tc_product(tmem, sA, sW + (uint32_t)((l - 2) * kMatBytes), false, bar_a, parity, a.error)) {
+    tc_issue(tmem, sA, sW + (uint32_t)((l - 2) * kMatBytes), false, bar_a);
+    // gelu'(z_{l-1}) of this thread's features, loaded while the product runs
+#pragma unroll
+    for (int q = 0; q < 8; ++q) load8(grow + (l - 2) * H + hf * 64 + q * 8, live, gz + q * 8);
+    if (!tc_wait(bar_a, parity, a.error)) {
       failed = true;
       break;
     }
-    for (int c = 2 * hf; c < 2 * hf + 2; ++c) {
-      float v[32], zz[32];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) load8(zrow + (l - 2) * H + c * 32 + q * 8, live, zz + q * 8);
+    for (int cc = 0; cc < 2; ++cc) {
+      const int c = 2 * hf + cc;
+      float v[32];
       tmem_ld32(tmem_at(tmem, c), v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = live ? v[j] * gelu_grad(zz[j]) : 0.f;
+      for (int j = 0; j < 32; ++j) v[j] = live ? v[j] * gz[cc * 32 + j] : 0.f;
       if (live) {
         float4* dd = reinterpret_cast<float4*>(a.dz + (((int64_t)m * 4 + (l - 2)) * a.n + p) * H + c * 32);
 #pragma unroll
@@ -391,7 +441,7 @@ __global__ void __launch_bounds__(kT, 1) mlp_backward_tc05_kernel(TrainTcArgs a)
 // (in, b)) are transposed into shared memory; the chunks accumulate in TMEM.
 // Staging: thread = (feature f = tid % 128, half of the chunk), 8 samples
 // packed per 16-byte store.  Writes the slice's partial dW_l and db_l.
-__global__ void __launch_bounds__(kT) mlp_wgrad_tc05_kernel(TrainTcArgs a) {
+__global__ void __launch_bounds__(kT, 3) mlp_wgrad_tc05_kernel(TrainTcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = align1024(smem_raw);
   const int tid = threadIdx.x, f = tid & 127, hf = tid >> 7;
@@ -417,17 +467,25 @@ __global__ void __launch_bounds__(kT) mlp_wgrad_tc05_kernel(TrainTcArgs a) {
   const float* D = a.dz + (((int64_t)m * 4 + (l - 1)) * a.n) * H;      // dz_l [n][128]
   const float* Z = a.z + (int64_t)m * a.n * 4 * H + (l - 2) * H;        // z_{l-1} of sample b at Z[b * 512]
   for (int64_t c0 = r0; c0 < r1 && !failed; c0 += kTile) {
+    // groups of 8 samples; the loads of group g + 1 are in flight while
+    // group g is converted and stored (samples past r1 read as 0, gelu(0) = 0)
+    float dn[8], zn[8];
+    load_group(D, Z, c0 + hf * 64, r1, f, dn, zn);
+#pragma unroll
     for (int g = 0; g < 8; ++g) {
       const int b0 = hf * 64 + g * 8;
       float d[8], h[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const int64_t smp = c0 + b0 + j;
-        d[j] = smp < r1 ? D[smp * H + f] : 0.f;
-        h[j] = smp < r1 ? gelu(Z[smp * 4 * H + f]) : 0.f;
+        d[j] = dn[j];
+        h[j] = zn[j];
       }
+      if (g < 7) load_group(D, Z, c0 + b0 + 8, r1, f, dn, zn);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) bsum += d[j];
+      for (int j = 0; j < 8; ++j) {
+        h[j] = gelu(h[j]);
+        bsum += d[j];
+      }
       store_bf16x8(smem + kGA, f, b0, d);
       store_bf16x8(smem + kGB, f, b0, h);
     }
