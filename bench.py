@@ -362,7 +362,9 @@ def run_config4(ens, torch, stream, dev, m=1024):
                          timeout_s=900.0)
         ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, n, C, y0, (0.0, 1.0), ens.ENS_RKCK45, t)
         try:
-            ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1 if prec == ens.ENS_FP64 else 2,
+            # measured on the 1024 x 1024 grid: FP64 26.6 s at 8 warps/SM (27.8 s at 4); the split-precision
+            # kernel, latency-bound across its mixed FP32/FP64 pipes, 1.14 s at 24 warps/SM (1.69 s at 8)
+            ens.ens_set_launch(ctx, ens.make_launch(block=256, blocks_per_sm=1 if prec == ens.ENS_FP64 else 3,
                                                     cost_order=1))
             if prec == ens.ENS_FP32_COMP:
                 ens.ens_solve(ctx, stream)          # warm-up (the FP64 kernel is warm already)
