@@ -370,3 +370,19 @@ def test_km_fp32_compensated_error_against_fp64_oracle():
               f"fp64 median {report[tol][1]:.2e} p90 {report[tol][3]:.2e} | steps ratio {report[tol][4]:.3f}")
         assert np.median(e32) < 3 * np.median(e64) + 1e-6
         assert np.percentile(e32, 90) < 3 * np.percentile(e64, 90) + 1e-5
+
+
+def test_km_fp32_compensated_launch_shapes_are_bitwise_identical():
+    """The split-precision kernel gives the same bits under every launch shape,
+    including the high-occupancy persistent shapes (24 warps/SM) that the
+    1024 x 1024 benchmark run uses."""
+    km = W.km(40, 50, n_phases=3)          # 2,000 systems
+    kw = dict(prec=ens.ENS_FP32_COMP, rtol=1e-8, atol=1e-8)
+    ref = _km_gpu(km, launch=ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=128), **kw)
+    assert ref["sync"] == ens.ENS_OK and np.all(ref["status"] == 0)
+    for L in (ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=256, blocks_per_sm=3, cost_order=1),
+              ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=128, blocks_per_sm=6, use_graph=1),
+              ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=32, blocks_per_sm=1)):
+        g = _km_gpu(km, launch=L, **kw)
+        for k in ("y", "acc", "nacc", "nrej", "nrhs", "status", "dt"):
+            assert np.array_equal(g[k], ref[k], equal_nan=True), (k, L.as_dict())
