@@ -107,6 +107,37 @@ def km(m_pa: int = 362, m_f: int = 362, n_phases: int = 64, pa_max: float = 2.0e
                 shape=(m_pa, m_f))
 
 
+def km_frequency_response(n_f: int = 46080, pA1: float = 1.5e5, f_min: float = 2.0e4, f_max: float = 1.0e6,
+                          n_transient: int = 1024, n_recorded: int = 64, RE: float = 10e-6, tol: float = 1e-10,
+                          liquid: dict | None = None):
+    """The Keller-Miksis frequency-response workload of Sec. 4.2: P_A1 =
+    1.5 bar, P_A2 = 0, theta = 0, R_E = 10 um, n_f values of f1 log-spaced
+    over 20 kHz - 1 MHz; n_transient phases are integrated and discarded,
+    the maxima of the next n_recorded phases are kept (the paper: 1024 and
+    64, curves of up to 46,080 frequencies)."""
+    f = logspace(f_min, f_max, n_f)
+    n = n_f
+    phys = dict(pA1=np.full(n, pA1), f1=f, pA2=np.zeros(n), f2=np.zeros(n), theta=np.zeros(n),
+                RE=np.full(n, RE))
+    y0 = np.stack([np.ones(n), np.zeros(n)])
+    tols = Tolerances(rtol=tol, atol=tol, dt0=1e-2, dt_min=1e-14, dt_max=1e-1,
+                      n_phases=n_transient + n_recorded, phase_len=1.0, t0=0.0, t1=1.0)
+    return dict(phys=phys, liquid=dict(liquid or WATER_25C), y0=y0, tol=tols, n_transient=n_transient)
+
+
+def km_dual(m_pa: int = 362, m_f: int = 362, n_phases: int = 64, amp_ratio: float = 0.5, freq_ratio: float = 2.0,
+            theta: float = 0.0, **kw):
+    """The p_A x f sweep of km() with a second driving component: P_A2 =
+    amp_ratio * P_A1 at f2 = freq_ratio * f1 with phase shift theta (the
+    dual-frequency form of the Keller-Miksis forcing, Sec. 4.2)."""
+    w = km(m_pa, m_f, n_phases=n_phases, **kw)
+    ph = w["phys"]
+    ph["pA2"] = amp_ratio * ph["pA1"]
+    ph["f2"] = freq_ratio * ph["f1"]
+    ph["theta"] = np.full(ph["pA1"].size, theta)
+    return w
+
+
 def prv(n: int = 262144, q_min: float = 0.2, q_max: float = 10.0, t1: float = 1024.0,
         tol: float = 1e-10):
     """Pressure-relief-valve q sweep: params (5, n) = (q, kappa, delta, beta, r)."""
