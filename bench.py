@@ -260,6 +260,8 @@ def run_ours(args):
         secondary["km_lyapunov_362x362"] = run_lyapunov(ens, torch, stream, dev, C_d, km, launch)
         secondary["km_dopri5_362x362"] = run_dopri5(ens, torch, stream, dev, ctx, C_d, y0_d, km, tol, launch,
                                                     total_ms / args.steps)
+        secondary["km_fp32x2_362x362"] = run_fp32x2(ens, torch, stream, dev, ctx, C_d, y0_d, km, tol,
+                                                    total_ms / args.steps)
         secondary["km_surrogate_screen"] = run_screen(ens, torch, stream, dev, ctx, km, total_ms / args.steps,
                                                       steps_local / args.steps, args)
 
@@ -592,6 +594,44 @@ def run_dual_frequency(ens, torch, stream, dev, launch):
     return res
 
 
+def run_fp32x2(ens, torch, stream, dev, ck_ctx, C_d, y0_d, km, tol, ck_ms):
+    """The headline sweep in double-float arithmetic (ENS_FP32X2: pairs of
+    floats on the FP32 pipes, time and forcing in FP64): time, speedup over
+    the FP64 solve and the per-system difference of the per-period maxima
+    from the FP64 solve's."""
+    n = km["phys"]["pA1"].size
+    t = km["tol"]
+    tol2 = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
+                        n_phases=t.n_phases, phase_len=t.phase_len, prec=ens.ENS_FP32X2, timeout_s=900.0)
+    ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, n, C_d, y0_d, (0.0, 1.0), ens.ENS_RKCK45, tol2)
+    try:
+        # 7 warps/SM measured best (6: 1.80 s, 7: 1.79 s, 8: 1.97 s, 12: 2.71 s)
+        ens.ens_set_launch(ctx, ens.make_launch(block=224, blocks_per_sm=1, cost_order=1))
+        ens.ens_solve(ctx, stream)
+        ens.ens_sync(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ens.ens_solve(ctx, stream)
+        e1.record(stream)
+        st = ens.ens_sync(ctx)
+        ms = e0.elapsed_time(e1)
+        nacc = ens.ens_read(ctx, ens.ENS_NSTEPS)
+        nrej = ens.ens_read(ctx, ens.ENS_NREJ)
+        acc = ens.ens_read(ctx, ens.ENS_ACC)
+        kms = ens.ens_kernel_ms(ctx)
+    finally:
+        ens.ens_destroy(ctx)
+    ref = ens.ens_read(ck_ctx, ens.ENS_ACC)
+    rel = np.abs(acc[0::2] - ref[0::2]).max(axis=0) / np.abs(ref[0::2]).max(axis=0)
+    return {"ms": ms, "kernel_ms": kms, "status": st, "accepted_steps": float(nacc.sum()),
+            "trials": float(nacc.sum() + nrej.sum()), "value": float(nacc.sum()) / (ms / 1e3),
+            "unit": "system-steps/s", "speedup_vs_fp64": ck_ms / ms,
+            "launch": {"block": 224, "blocks_per_sm": 1, "cost_order": 1},
+            "per_period_max_rel_diff_vs_fp64": {"median": float(np.median(rel)),
+                                                "p90": float(np.percentile(rel, 90)),
+                                                "frac_below_1e-8": float(np.mean(rel < 1e-8))}}
+
+
 def run_secondary(ens, torch, stream, dev):
     """The other hot-path workloads, timed the same way (one launch each after
     a warm-up): RK4 peak-calibration x' = x^2 - p (Sec. 3), RK4 Lorenz
@@ -770,6 +810,20 @@ def run_profile_case(case: str):
         ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
                              ens.ENS_RKCK45, tol)
         ens.ens_set_launch(ctx, ens.make_launch(block=256, blocks_per_sm=1, cost_order=0))
+    elif case == "km_fp32x2":
+        # 16,384 stratified systems of the 362 x 362 sweep, 2 periods, tol 1e-10, double-float
+        km = km_slice(1, 0, n_phases=2)
+        idx = W.subsample(km["phys"]["pA1"].size, 16384)
+        km = W.take(km, idx)
+        ph = km["phys"]
+        C = ens.ens_km_coefficients(ph["pA1"], ph["f1"], ph["pA2"], ph["f2"], ph["theta"], ph["RE"],
+                                    km["liquid"])
+        t = km["tol"]
+        tol = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
+                           n_phases=t.n_phases, phase_len=t.phase_len, prec=ens.ENS_FP32X2)
+        ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
+                             ens.ENS_RKCK45, tol)
+        ens.ens_set_launch(ctx, ens.make_launch(block=224, blocks_per_sm=1, cost_order=0))
     elif case == "mlp_screen":
         import torch
         m = ens.ens_mlp_create(4, W.SEED)
@@ -828,7 +882,7 @@ def run_profile_case(case: str):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile", default=None,
-                    help="run one small case for ncu (km, km_full64, km_full2, km_fp32c, mlp_screen, mlp_train, "
+                    help="run one small case for ncu (km, km_full64, km_full2, km_fp32c, km_fp32x2, mlp_screen, mlp_train, "
                          "prv, x2p, lorenz)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)

@@ -95,8 +95,14 @@ typedef enum { ENS_RK4 = 0, ENS_RKCK45 = 1, ENS_DOPRI5 = 2 } ens_solver;
  *   ENS_FP32_COMP    right-hand side and stage sums in float with compensated
  *                    (Kahan) stage combination and a float-pair (hi + lo)
  *                    state; time, error norm, controller and event root in
- *                    double (Keller-Miksis / Cash-Karp only).               */
-typedef enum { ENS_FP64 = 0, ENS_FP32_COMP = 1, ENS_FP64_STRICT = 2 } ens_precision;
+ *                    double (Keller-Miksis / Cash-Karp only).
+ *   ENS_FP32X2       double-float: every value of the step (state, stages,
+ *                    right-hand side, error estimate, controller) is a pair
+ *                    of floats, about 48 significant bits, on the FP32
+ *                    pipes; the time, the step and the forcing sin / cos are
+ *                    double.  Keller-Miksis phase mode with Cash-Karp and
+ *                    C10 = 21/5 only (else ENS_ENOTSUP from ens_solve).     */
+typedef enum { ENS_FP64 = 0, ENS_FP32_COMP = 1, ENS_FP64_STRICT = 2, ENS_FP32X2 = 3 } ens_precision;
 
 /* Per-system status bits (ENS_STATUS). */
 enum {

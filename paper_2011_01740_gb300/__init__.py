@@ -28,7 +28,7 @@ LIB_PATH = os.path.join(_HERE, "libens.so")
 ENS_OK, ENS_EINVAL, ENS_ENOMEM, ENS_ECUDA, ENS_ETIMEOUT, ENS_ESYSTEM, ENS_ENOTSUP = range(7)
 ENS_SYS_TOY_X2P, ENS_SYS_LORENZ, ENS_SYS_KELLER_MIKSIS, ENS_SYS_RELIEF_VALVE, ENS_SYS_KELLER_MIKSIS_TANGENT = range(5)
 ENS_RK4, ENS_RKCK45, ENS_DOPRI5 = 0, 1, 2
-ENS_FP64, ENS_FP32_COMP, ENS_FP64_STRICT = 0, 1, 2
+ENS_FP64, ENS_FP32_COMP, ENS_FP64_STRICT, ENS_FP32X2 = 0, 1, 2, 3
 ENS_SYS_DT_UNDERFLOW, ENS_SYS_MAX_STEPS, ENS_SYS_NONFINITE = 1, 2, 4
 ENS_SYS_EVENT_NO_CONVERGE, ENS_SYS_TIMEOUT = 8, 16
 ENS_STATE, ENS_ACC, ENS_STATUS, ENS_NSTEPS, ENS_NREJ, ENS_NRHS, ENS_TIME, ENS_DT = range(8)

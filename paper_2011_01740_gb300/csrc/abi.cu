@@ -17,6 +17,7 @@ namespace ens {
 cudaError_t launch_rk4(int sys, bool strict, const Rk4Args& a, int block, cudaStream_t s);
 cudaError_t launch_ck45(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_ck45_fp32c(unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
+cudaError_t launch_ck45_df(unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_order(const int64_t* steps, int64_t n, int32_t* order, unsigned* hist,
                          cudaStream_t s);
 cudaError_t launch_rhs_eval(int sys, unsigned flags, int64_t n, const double* P, const double* t,
@@ -224,13 +225,13 @@ ens_status check_tol(ens_ctx* c, ens_solver solver, ens_system sys, const ens_to
     set_err(c, "the relief valve runs in event mode (n_phases must be 0)");
     return ENS_ENOTSUP;
   }
-  if (t.prec == ENS_FP32_COMP &&
+  if ((t.prec == ENS_FP32_COMP || t.prec == ENS_FP32X2) &&
       !(sys == ENS_SYS_KELLER_MIKSIS && t.n_phases > 0 && solver == ENS_RKCK45)) {
-    set_err(c, "ENS_FP32_COMP is implemented for the Keller-Miksis phase mode with Cash-Karp");
+    set_err(c, "ENS_FP32_COMP and ENS_FP32X2 are implemented for the Keller-Miksis phase mode with Cash-Karp");
     return ENS_ENOTSUP;
   }
-  if (t.prec != ENS_FP64 && t.prec != ENS_FP32_COMP) {
-    set_err(c, "adaptive solves support ENS_FP64 and ENS_FP32_COMP");
+  if (t.prec != ENS_FP64 && t.prec != ENS_FP32_COMP && t.prec != ENS_FP32X2) {
+    set_err(c, "adaptive solves support ENS_FP64, ENS_FP32_COMP and ENS_FP32X2");
     return ENS_ENOTSUP;
   }
   return ENS_OK;
@@ -239,6 +240,13 @@ ens_status check_tol(ens_ctx* c, ens_solver solver, ens_system sys, const ens_to
 uint64_t timeout_ns(const ens_tol& t) {
   const double s = t.timeout_s > 0.0 ? t.timeout_s : 600.0;
   return (uint64_t)(s * 1e9);
+}
+
+// the adaptive kernel of the context's precision
+cudaError_t launch_adaptive(const ens_ctx* c, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s) {
+  if (c->tol.prec == ENS_FP32_COMP) return launch_ck45_fp32c(c->km_flags, a, L, s);
+  if (c->tol.prec == ENS_FP32X2) return launch_ck45_df(c->km_flags, a, L, s);
+  return launch_ck45(c->sys, c->km_flags, a, L, s);
 }
 
 AdaptArgs adapt_args(ens_ctx* c) {
@@ -319,6 +327,10 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int sh
     c->kev_recorded = true;
     return ENS_OK;
   }
+  if (c->tol.prec == ENS_FP32X2 && (c->km_flags & kKmGeneralExponent)) {
+    set_err(c, "ENS_FP32X2 needs C10 = 21/5 (polytropic exponent 1.4) in every system");
+    return ENS_ENOTSUP;
+  }
   AdaptArgs a = adapt_args(c);
   if (shorten > 0) {
     if (a.n_phases > 0) a.n_phases = std::min<int32_t>(a.n_phases, shorten);
@@ -339,8 +351,7 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int sh
     p.rtol = p.rtol > kPilotTol ? p.rtol : kPilotTol;
     p.atol = p.atol > kPilotTol ? p.atol : kPilotTol;
     AdaptLaunch PL{(c->n + 127) / 128, 128};
-    cudaError_t e = c->tol.prec == ENS_FP32_COMP ? launch_ck45_fp32c(c->km_flags, p, PL, s)
-                                                 : launch_ck45(c->sys, c->km_flags, p, PL, s);
+    cudaError_t e = launch_adaptive(c, p, PL, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "pilot launch");
     e = launch_order(c->nacc, c->n, c->order, c->hist, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "order launch");
@@ -349,8 +360,7 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int sh
   }
   AdaptLaunch AL = adapt_launch(c, L);
   ENS_CUDA(c, record_kernel_event(c, 0, s));
-  cudaError_t e = c->tol.prec == ENS_FP32_COMP ? launch_ck45_fp32c(c->km_flags, a, AL, s)
-                                               : launch_ck45(c->sys, c->km_flags, a, AL, s);
+  cudaError_t e = launch_adaptive(c, a, AL, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "adaptive launch");
   ENS_CUDA(c, record_kernel_event(c, 1, s));
   c->kev_recorded = true;

@@ -1,0 +1,30 @@
+// df_host.cpp -- host build of the double-float arithmetic (df.cuh) and of
+// the double-float Keller-Miksis right-hand side (km_df.cuh) for the CPU
+// tests (test_df_host.py); compiled with g++ -ffp-contract=off.
+#include <cmath>
+#include <cstdint>
+#include "km_df.cuh"
+using namespace ens::df;
+extern "C" {
+// C: [13][n] SoA like the library; fs, fc: forcing values; out: y2'
+void accel_df(int n, const double* C, const double* fs, const double* fc, const double* y1, const double* y2, double* out) {
+  for (int i = 0; i < n; ++i) {
+    KmDFCoef k;
+    k.load(C, n, i);
+    DF a = k.accel(from_double(fs[i]), from_double(fc[i]), from_double(y1[i]), from_double(y2[i]));
+    out[i] = to_double(a);
+  }
+}
+void prims(int n, const double* a, const double* b, double* out) {
+  // out[6][n]: add, mul, rcp(a), inv5(a), from/to round trip of a, a - b
+  for (int i = 0; i < n; ++i) {
+    DF x = from_double(a[i]), y = from_double(b[i]);
+    out[i] = to_double(add(x, y));
+    out[n + i] = to_double(mul(x, y));
+    out[2 * n + i] = to_double(rcp(x));
+    out[3 * n + i] = to_double(inv_fifth_root(x));
+    out[4 * n + i] = to_double(x);
+    out[5 * n + i] = to_double(sub(x, y));
+  }
+}
+}

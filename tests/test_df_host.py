@@ -1,0 +1,97 @@
+"""Host checks of the double-float arithmetic of the ENS_FP32X2 kernel
+(csrc/df.cuh) and of its Keller-Miksis right-hand side (csrc/km_df.cuh),
+built for the CPU with g++ (every function there is __host__ __device__).
+
+The error bounds are those of the double-word algorithms (Joldes, Muller &
+Popescu, ACM TOMS 44(2), 2017) in units of u^2 = 2^-48; the right-hand side
+is checked against the float64 oracle (Sec. 4.2 equations) relative to the
+magnitude of the terms that cancel in N_KM."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_01740_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2011_01740_gb300", "csrc")
+U2 = 2.0 ** -48
+P = ctypes.POINTER(ctypes.c_double)
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    out = str(tmp_path_factory.mktemp("dfhost") / "df_host.so")
+    subprocess.run([gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", f"-I{CSRC}",
+                    os.path.join(HERE, "df_host.cpp"), "-o", out], check=True)
+    return ctypes.CDLL(out)
+
+
+def _p(a):
+    return np.ascontiguousarray(a, dtype=np.float64).ctypes.data_as(P)
+
+
+def _prims(lib, a, b):
+    out = np.zeros((6, a.size))
+    lib.prims(a.size, _p(a), _p(b), out.ctypes.data_as(P))
+    return out
+
+
+def _rel(x, r):
+    return np.abs(x - r) / np.abs(r)
+
+
+def test_double_word_operations_meet_their_error_bounds(lib):
+    rng = np.random.default_rng(2)
+    n = 100_000
+    a = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-10, 10, n)
+    b = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-10, 10, n)
+    oa, ob = _prims(lib, a, b), _prims(lib, b, a)
+    xa, xb = oa[4], ob[4]                       # the pairs as doubles (exact)
+    assert _rel(xa, a).max() <= 2.0 * U2        # double -> pair -> double
+    assert _rel(oa[1], xa * xb).max() <= 5.0 * U2 + 2.0 ** -52
+    # accurate addition: absolute error below 3 u^2 of the operands' magnitude
+    assert (np.abs(oa[0] - (xa + xb)) / (np.abs(xa) + np.abs(xb))).max() <= 3.0 * U2 + 2.0 ** -52
+    assert np.array_equal(oa[5], _prims(lib, a, -b)[0])          # x - y = x + (-y)
+    assert _rel(oa[2], 1.0 / xa).max() <= 4.0 * U2 + 2.0 ** -52
+    x = 10.0 ** rng.uniform(-2, 2, n)
+    ox = _prims(lib, x, x)
+    assert _rel(ox[3], ox[4] ** -0.2).max() <= 4.0 * U2 + 2.0 ** -52
+
+
+def test_cancellation_is_exact_when_the_result_is_representable(lib):
+    # (1 + 2^-30) - 1 = 2^-30 exactly: a float cannot hold 1 + 2^-30, the pair can
+    a = np.array([1.0 + 2.0 ** -30, 3.0 + 2.0 ** -40])
+    b = np.array([1.0, 3.0])
+    out = _prims(lib, a, b)
+    assert np.array_equal(out[5], np.array([2.0 ** -30, 2.0 ** -40]))
+
+
+def test_keller_miksis_right_hand_side_matches_the_oracle(lib):
+    rng = np.random.default_rng(1)
+    n = 50_000
+    phys = dict(pA1=rng.uniform(0, 2e5, n), f1=10 ** rng.uniform(np.log10(2e4), 6, n), pA2=rng.uniform(0, 1e5, n),
+                f2=10 ** rng.uniform(np.log10(2e4), 6, n), theta=rng.uniform(0, 6.28, n), RE=np.full(n, 10e-6))
+    C = np.ascontiguousarray(oracle.km_coefficients(phys["pA1"], phys["f1"], phys["pA2"], phys["f2"],
+                                                    phys["theta"], phys["RE"], oracle.liquid(**W.WATER_25C)))
+    t = rng.uniform(0, 1, n)
+    y1, y2 = rng.uniform(0.2, 5.0, n), rng.uniform(-3.0, 3.0, n)
+    ref = oracle.rhs(oracle.KM, C, t, np.vstack([y1, y2]))[1]
+    # the forcing sums of the oracle's equation, handed over as doubles
+    w = 2 * np.pi
+    fs = C[5] * np.sin(w * t) + C[6] * np.sin(w * C[11] * t + C[12])
+    fc = C[7] * np.cos(w * t) + C[8] * np.cos(w * C[11] * t + C[12])
+    out = np.zeros(n)
+    lib.accel_df(n, _p(C), _p(fs), _p(fc), _p(y1), _p(y2), out.ctypes.data_as(P))
+    D = y1 * (1 - C[9] * y2) + C[4] * C[9]
+    scale = (np.abs(C[0] + C[1] * y2) * y1 ** -4.2 + np.abs(C[2] * (1 + C[9] * y2)) + np.abs(C[3] + C[4] * y2) / y1
+             + np.abs(fs * (1 + C[9] * y2)) + np.abs(y1 * fc) + 1.5 * y2 ** 2) / np.abs(D)
+    err = np.abs(out - ref) / scale
+    assert np.percentile(err, 99) < 1e-13 and err.max() < 5e-13, (np.percentile(err, 99), err.max())
