@@ -203,12 +203,10 @@ ens_status check_train_err(ens_mlp* m) {
   return ENS_OK;
 }
 
-bool g_attr_set = false;
-
 ens_status set_smem_attrs(ens_mlp* m) {
-  if (g_attr_set) return ENS_OK;
-  MLP_CUDA(m, mlp::set_smem_limits());
-  g_attr_set = true;
+  // once per process (thread-safe static initialisation)
+  static const cudaError_t attr = mlp::set_smem_limits();
+  MLP_CUDA(m, attr);
   return ENS_OK;
 }
 

@@ -221,13 +221,10 @@ __global__ void mlp_reduce_members_kernel(int64_t n, int members, const float* o
 cudaError_t launch_screen_tc05(int64_t n, int members, const float* x, const float* master, const __nv_bfloat16* wbf,
                                float* out, unsigned* error, float* mean, float* stdv, float* p1, int sms,
                                cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_screen_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kTcSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // once per process (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(mlp_screen_tc05_kernel,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (attr != cudaSuccess) return attr;
   if (n == 0) return cudaSuccess;
   TcArgs a{};
   a.n = n;

@@ -518,17 +518,17 @@ __global__ void __launch_bounds__(kT, 3) mlp_wgrad_tc05_kernel(TrainTcArgs a) {
 }
 
 cudaError_t launch_train_tc05(int step, const TrainTcArgs& a, int splits, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  // once per process (thread-safe static initialisation)
+  static const cudaError_t attr = [] {
     cudaError_t e = cudaFuncSetAttribute(mlp_forward_train_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kFSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mlp_backward_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mlp_wgrad_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+    return e;
+  }();
+  if (attr != cudaSuccess) return attr;
   const int64_t tiles = (a.n + kTile - 1) / kTile;
   if (a.n <= 0 || tiles > 0x7fffffffLL || a.members < 1 || a.members > kMaxMembers) return cudaErrorInvalidValue;
   if (step == 0) {
