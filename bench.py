@@ -246,7 +246,9 @@ def run_ours(args):
                 "kernel_ms": kernel_ms, "duration_source": kernel_src,
                 "fp64_inst_per_trial": FP64_INST_PER_KM_TRIAL,
                 "fp64_issue_frac": (FP64_INST_PER_KM_TRIAL * trials_local / (kernel_ms / 1e3) / FP64_INST_PEAK
-                                    if FP64_INST_PER_KM_TRIAL else None)}
+                                    if FP64_INST_PER_KM_TRIAL else None),
+                # the share of the work spent on accepted steps (rejected trials are discarded)
+                "useful_frac": (steps_local / args.steps) / trials_local if trials_local else None}
 
     secondary = {}
     # single-GPU secondaries: at N > 1 they would hold every rank's GPU while
@@ -718,9 +720,17 @@ def cpu_baseline(km, seconds: float):
         steps, el = _oracle_sample_solve(km, W.subsample(n, k))
     # one host core, for comparison with the paper's single-core CPU runs
     s1, e1 = _oracle_sample_solve(km, W.subsample(n, 256), nthreads=1)
+    # and the x' = x^2 - p RK4 calibration (21 flop per step, Sec. 3) on one core
+    cal = W.x2p(4096)
+    t0 = time.perf_counter()
+    oracle.rk4_solve(oracle.X2P, cal["params"], cal["y0"], 0.0, cal["dt"], cal["nsteps"], nthreads=1)
+    ec = time.perf_counter() - t0
+    cal_sps = 4096 * cal["nsteps"] / ec
     return {"value": steps / el, "unit": "system-steps/s", "cores": oracle.max_threads(),
             "kind": "oracle", "sample": f"{k} of {n} systems (stratified, seed {W.SEED}), 64 periods",
-            "seconds": el, "single_core_value": s1 / e1, "single_core_sample": "256 systems, 1 thread"}
+            "seconds": el, "single_core_value": s1 / e1, "single_core_sample": "256 systems, 1 thread",
+            "x2p_rk4_single_core": {"value": cal_sps, "unit": "system-steps/s", "gflops": cal_sps * 21 / 1e9,
+                                    "sample": f"4096 systems x {cal['nsteps']} steps, 1 thread"}}
 
 
 def run_reference(args):
