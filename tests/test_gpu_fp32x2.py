@@ -135,3 +135,20 @@ def test_general_polytropic_exponent_is_not_supported():
         assert e.value.status == ens.ENS_ENOTSUP
     finally:
         ens.ens_destroy(ctx)
+
+
+def test_status_words():
+    """The same per-system status handling as the FP64 kernel: the trial budget,
+    an unreachable tolerance (step underflow) and the wall-clock budget."""
+    km = W.km(3, 4, n_phases=2)
+    g = _km(km, max_steps=5)
+    assert np.all((g["status"] & ens.ENS_SYS_MAX_STEPS) > 0)
+    assert np.all(g["nacc"] + g["nrej"] == 5)
+    assert np.all(np.isnan(g["acc"][2:]))           # phase 1 never completed
+    assert g["sync"] == ens.ENS_ESYSTEM
+    g = _km(km, rtol=1e-30, atol=1e-30, dt_min=1e-6)
+    forced = km["phys"]["pA1"] > 0
+    assert np.all((g["status"][forced] & ens.ENS_SYS_DT_UNDERFLOW) > 0)
+    g = _km(W.km(20, 20, n_phases=64), timeout_s=1e-6)
+    assert g["sync"] == ens.ENS_ETIMEOUT
+    assert np.all((g["status"] & ens.ENS_SYS_TIMEOUT) > 0)
