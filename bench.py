@@ -351,9 +351,10 @@ def run_e2e(ens, ctx, km, stream, args, dist=None, dev=None, world=1):
 
 
 def run_config4(ens, torch, stream, dev, m=1024):
-    """1024 x 1024 Keller-Miksis grid, 64 periods, twice: plain FP64 (tol
-    1e-10) and the split-precision FP32 variant (tol 1e-8); the FP32 run's
-    per-period maxima against the FP64 run's."""
+    """1024 x 1024 Keller-Miksis grid, 64 periods, three times: plain FP64 (tol
+    1e-10), the split-precision FP32 variant (tol 1e-8) and the double-float
+    variant (tol 1e-10); the variants' per-period maxima against the FP64
+    run's."""
     km = W.km(m, m, n_phases=64)
     ph = km["phys"]
     n = ph["pA1"].size
@@ -363,14 +364,17 @@ def run_config4(ens, torch, stream, dev, m=1024):
     stream.synchronize()
     res = {"systems": n}
     accs = {}
-    for name, prec, tol in (("fp64_tol1e-10", ens.ENS_FP64, 1e-10), ("fp32c_tol1e-8", ens.ENS_FP32_COMP, 1e-8)):
+    # launch shapes measured on this grid: FP64 26.6 s at 8 warps/SM (27.8 s at 4); the split-precision
+    # kernel, latency-bound across its mixed FP32/FP64 pipes, 1.14 s at 24 warps/SM (1.69 s at 8); the
+    # double-float kernel 10.1 s at 16 warps/SM (11.6 s at 7)
+    shapes = {ens.ENS_FP64: (256, 1), ens.ENS_FP32_COMP: (256, 3), ens.ENS_FP32X2: (256, 2)}
+    for name, prec, tol in (("fp64_tol1e-10", ens.ENS_FP64, 1e-10), ("fp32c_tol1e-8", ens.ENS_FP32_COMP, 1e-8),
+                            ("fp32x2_tol1e-10", ens.ENS_FP32X2, 1e-10)):
         t = ens.make_tol(rtol=tol, atol=tol, dt0=1e-2, dt_min=1e-14, dt_max=1e-1, n_phases=64, prec=prec,
                          timeout_s=900.0)
         ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, n, C, y0, (0.0, 1.0), ens.ENS_RKCK45, t)
         try:
-            # measured on the 1024 x 1024 grid: FP64 26.6 s at 8 warps/SM (27.8 s at 4); the split-precision
-            # kernel, latency-bound across its mixed FP32/FP64 pipes, 1.14 s at 24 warps/SM (1.69 s at 8)
-            ens.ens_set_launch(ctx, ens.make_launch(block=256, blocks_per_sm=1 if prec == ens.ENS_FP64 else 3,
+            ens.ens_set_launch(ctx, ens.make_launch(block=shapes[prec][0], blocks_per_sm=shapes[prec][1],
                                                     cost_order=1))
             if prec == ens.ENS_FP32_COMP:
                 ens.ens_solve(ctx, stream)          # warm-up (the FP64 kernel is warm already)
@@ -393,6 +397,12 @@ def run_config4(ens, torch, stream, dev, m=1024):
     res["fp32c_rel_err_per_period_max"] = {"median": float(np.median(rel)), "p90": float(np.percentile(rel, 90)),
                                            "p99": float(np.percentile(rel, 99))}
     res["speedup_fp32c_vs_fp64"] = res["fp64_tol1e-10"]["ms"] / res["fp32c_tol1e-8"]["ms"]
+    c = accs["fp32x2_tol1e-10"]
+    rel2 = np.abs(c - b).max(0) / np.abs(b).max(0)
+    res["fp32x2_rel_diff_per_period_max_vs_fp64"] = {"median": float(np.median(rel2)),
+                                                     "p90": float(np.percentile(rel2, 90)),
+                                                     "frac_below_1e-8": float(np.mean(rel2 < 1e-8))}
+    res["speedup_fp32x2_vs_fp64"] = res["fp64_tol1e-10"]["ms"] / res["fp32x2_tol1e-10"]["ms"]
     return res
 
 
