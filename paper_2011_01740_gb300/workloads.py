@@ -17,6 +17,12 @@ shapes below follow those sweeps):
                   logarithmic in [20 kHz, 1 MHz], f varying fastest; y = (1, 0)
                   at tau = 0; Cash-Karp at tol 1e-10; 64 forcing periods, max /
                   min radius per period (Sec. 4.2).
+  * ``km_frequency_response`` - the paper's own Keller-Miksis run: P_A1 =
+                  1.5 bar, P_A2 = 0, 46,080 values of f1 logarithmic in
+                  [20 kHz, 1 MHz], 1024 transient + 64 recorded periods
+                  (Sec. 4.2.1).
+  * ``km_dual`` - the ``km`` sweep with a second driving component,
+                  P_A2 = P_A1 / 2 at f2 = 2 f1.
   * ``prv``     - pressure relief valve, kappa = 1.25, delta = 10, beta = 20,
                   r = 0.8, q = linspace(0.2, 10, N), y = (0.2, 0, 0), t in
                   [0, 1024], tol 1e-10, event tolerance 1e-6 (Sec. 4.3).
