@@ -844,9 +844,10 @@ def run_profile_case(case: str):
         ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
                              ens.ENS_RKCK45, tol)
         ens.ens_set_launch(ctx, ens.make_launch(block=224, blocks_per_sm=1, cost_order=0))
-    elif case == "mlp_screen":
+    elif case in ("mlp_screen", "mlp_screen_mma"):
         import torch
         m = ens.ens_mlp_create(4, W.SEED)
+        ens.ens_mlp_set_screen_impl(m, 0 if case == "mlp_screen_mma" else 1)
         pa, f = W.screen_grid(512)
         n = pa.size
         x = torch.empty((n, 2), dtype=torch.float32, device="cuda")
@@ -902,8 +903,8 @@ def run_profile_case(case: str):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile", default=None,
-                    help="run one small case for ncu (km, km_full64, km_full2, km_fp32c, km_fp32x2, mlp_screen, mlp_train, "
-                         "prv, x2p, lorenz)")
+                    help="run one small case for ncu (km, km_full64, km_full2, km_fp32c, km_fp32x2, mlp_screen, "
+                         "mlp_screen_mma, mlp_train, prv, x2p, lorenz)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
