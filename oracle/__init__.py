@@ -30,10 +30,10 @@ _lock = threading.Lock()
 _lib = None
 
 # system identifiers (mirror the enum in oracle.c)
-X2P, LORENZ, KM, PRV, LINEAR, TPOW, BALL, KM_TAN = range(8)
+X2P, LORENZ, KM, PRV, LINEAR, TPOW, BALL, KM_TAN, FCOS = range(9)
 CASHKARP, DOPRI5 = 0, 1                     # Tol.method
-DIM = {X2P: 1, LORENZ: 3, KM: 2, PRV: 3, LINEAR: 1, TPOW: 1, BALL: 3, KM_TAN: 4}
-NPAR = {X2P: 1, LORENZ: 3, KM: 13, PRV: 5, LINEAR: 1, TPOW: 2, BALL: 2, KM_TAN: 13}
+DIM = {X2P: 1, LORENZ: 3, KM: 2, PRV: 3, LINEAR: 1, TPOW: 1, BALL: 3, KM_TAN: 4, FCOS: 1}
+NPAR = {X2P: 1, LORENZ: 3, KM: 13, PRV: 5, LINEAR: 1, TPOW: 2, BALL: 2, KM_TAN: 13, FCOS: 1}
 
 ST_DT_UNDERFLOW, ST_MAX_STEPS, ST_NONFINITE, ST_EVENT_NO_CONVERGE = 1, 2, 4, 8
 RING = 32

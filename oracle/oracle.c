@@ -49,7 +49,8 @@ enum {
     ORC_LINEAR = 4,   /* y' = lambda*y (test problem)    params: lambda            */
     ORC_TPOW = 5,     /* y' = c*t^k   (test problem)     params: k, c              */
     ORC_BALL = 6,     /* y1'=y2, y2'=-g, y3'=0 (test)    params: g, r              */
-    ORC_KM_TAN = 7    /* Keller-Miksis + tangent vector  params: C0..C12           */
+    ORC_KM_TAN = 7,   /* Keller-Miksis + tangent vector  params: C0..C12           */
+    ORC_FCOS = 8      /* y' = c cos(2 pi t) (test)       params: c                 */
 };
 
 /* per-system status bits */
@@ -71,6 +72,7 @@ int orc_dim(int sys)
     case ORC_TPOW: return 1;
     case ORC_BALL: return 3;
     case ORC_KM_TAN: return 4;
+    case ORC_FCOS: return 1;
     default: return 0;
     }
 }
@@ -86,6 +88,7 @@ int orc_npar(int sys)
     case ORC_TPOW: return 2;
     case ORC_BALL: return 2;
     case ORC_KM_TAN: return 13;
+    case ORC_FCOS: return 1;
     default: return 0;
     }
 }
@@ -195,6 +198,15 @@ static void rhs_tpow(const double *p, double t, const double *y, double *dy)
     dy[0] = p[1] * pow(t, p[0]);
 }
 
+/* Forced test problem of period 1 in t: y' = c cos(2 pi t), whose solution
+ * y0 + c sin(2 pi t) / (2 pi) has its extremes at t = 1/4 and 3/4 of every
+ * period; it pins the per-phase maximum / minimum rows of phase mode.       */
+static void rhs_fcos(const double *p, double t, const double *y, double *dy)
+{
+    (void)y;
+    dy[0] = p[0] * cos(2.0 * M_PI * t);
+}
+
 static void rhs_ball(const double *p, double t, const double *y, double *dy)
 {
     (void)t;
@@ -214,6 +226,7 @@ static void rhs(int sys, const double *p, double t, const double *y, double *dy)
     case ORC_LINEAR: rhs_linear(p, t, y, dy); break;
     case ORC_TPOW: rhs_tpow(p, t, y, dy); break;
     case ORC_BALL: rhs_ball(p, t, y, dy); break;
+    case ORC_FCOS: rhs_fcos(p, t, y, dy); break;
     default: break;
     }
 }

@@ -121,6 +121,73 @@ def test_km_equilibrium_without_driving():
     assert np.abs(r["y"][0] - 1.0).max() < 1e-9
 
 
+# ---------------------------------------------------------------------------
+# Phase mode: the per-phase maximum / minimum rows (Sec. 4.2, Sec. 4.2.1)
+# ---------------------------------------------------------------------------
+# The paper records, for every forcing period, the largest y1 seen at the
+# solver's own step points (no dense output), with tau restarting at 0 each
+# period.  The reading implemented: rows 2k and 2k+1 hold the maximum and the
+# minimum of y1 over phase k, taken over the accepted step points and the
+# phase-start state.  Three problems with closed-form answers pin it.
+
+def _phase_tol(n_phases, dt0=1e-2, dt_max=0.1, tol=1e-10):
+    return oracle.make_tol(rtol=tol, atol=tol, dt0=dt0, dt_min=1e-14, dt_max=dt_max,
+                           n_phases=n_phases, phase_len=1.0, t0=0.0)
+
+
+@pytest.mark.parametrize("c", [1.0, -1.0])
+def test_phase_rows_of_a_constant_slope(c):
+    """y' = c over 5 phases from y0: phase k runs from y0 + c k to
+    y0 + c (k + 1).  Row 2k (max) and row 2k+1 (min) are those two values in
+    the order the sign of c gives.  This fails if the rows are swapped or
+    shifted by one phase, and if the phase-start state is left out (the first
+    step point of a phase lies up to dt_max = 0.1 past it)."""
+    y0, P = 0.5, 5
+    r = oracle.cashkarp_solve(oracle.TPOW, [[0.0], [c]], [[y0]], _phase_tol(P))
+    assert r["status"][0] == 0
+    acc = r["acc"][:, 0]
+    assert acc.size == 2 * P
+    for k in range(P):
+        start, end = y0 + c * k, y0 + c * (k + 1)
+        assert abs(acc[2 * k] - max(start, end)) < 1e-12, (k, acc[2 * k])
+        assert abs(acc[2 * k + 1] - min(start, end)) < 1e-12, (k, acc[2 * k + 1])
+    assert abs(r["y"][0, 0] - (y0 + c * P)) < 1e-12
+
+
+def test_phase_rows_restart_tau_every_phase():
+    """y' = tau with tau reset to 0 at each phase start adds exactly 1/2 per
+    phase, so phase k spans [y0 + k/2, y0 + (k + 1)/2].  Without the reset,
+    phase k would add (2k + 1)/2 and the rows of phases 1.. would be off."""
+    y0, P = 0.25, 4
+    r = oracle.cashkarp_solve(oracle.TPOW, [[1.0], [1.0]], [[y0]], _phase_tol(P))
+    assert r["status"][0] == 0
+    acc = r["acc"][:, 0]
+    for k in range(P):
+        assert abs(acc[2 * k] - (y0 + (k + 1) / 2.0)) < 1e-12, (k, acc[2 * k])
+        assert abs(acc[2 * k + 1] - (y0 + k / 2.0)) < 1e-12, (k, acc[2 * k + 1])
+    assert abs(r["y"][0, 0] - (y0 + P / 2.0)) < 1e-12
+
+
+def test_phase_rows_of_a_periodic_forcing():
+    """y' = cos(2 pi tau): y = y0 + sin(2 pi tau) / (2 pi) peaks at tau = 1/4
+    and bottoms out at 3/4, inside each phase.  With dt0 = dt_max = 1/64 every
+    step is 1/64 (the local error is far below the tolerance, so the
+    controller keeps the largest step), the step points hit 1/4 and 3/4
+    exactly, and each phase's rows are y0 + 1/(2 pi) and y0 - 1/(2 pi) to
+    the integration error.  Recording only phase ends would give y0 in both
+    rows."""
+    y0, P = 0.125, 3
+    r = oracle.cashkarp_solve(oracle.FCOS, [[1.0]], [[y0]], _phase_tol(P, dt0=1 / 64, dt_max=1 / 64, tol=1e-8))
+    assert r["status"][0] == 0
+    assert r["nacc"][0] == 64 * P and r["nrej"][0] == 0
+    acc = r["acc"][:, 0]
+    amp = 1.0 / (2.0 * math.pi)
+    for k in range(P):
+        assert abs(acc[2 * k] - (y0 + amp)) < 1e-9, (k, acc[2 * k])
+        assert abs(acc[2 * k + 1] - (y0 - amp)) < 1e-9, (k, acc[2 * k + 1])
+    assert abs(r["y"][0, 0] - y0) < 1e-9
+
+
 def test_km_tangent_jacobian_matches_central_differences():
     """The hand-derived Jacobian of the tangent system against central
     differences of the plain Keller-Miksis right-hand side (random driven
@@ -454,6 +521,54 @@ def test_prv_grazing_impact_from_a_recorded_state():
     assert r["status"][0] == 0
     assert int(r["acc"][34, 0]) == 1
     assert r["acc"][32, 0] == 0.0
+
+
+def test_prv_sticking_interval_has_the_closed_form():
+    """Sticking (a reading; the paper is silent): after an impact whose
+    rebound cannot leave the event band, the valve rests on the seat
+    (y1 = y2 = 0) and y3' = beta q exactly, until y3 reaches delta at
+    t_lift = t + (delta - y3) / (beta q).
+
+    The valve starts on the seat with y3 = 5 < delta: the seat force pushes it
+    down, the first step is cut back to an impact with a tiny rebound, and it
+    sticks.  Before t_lift = (delta - 5) / (beta q) = 0.25 the state must be
+    (0, 0, 5 + beta q t).  After it, the valve leaves the seat from
+    (0, 0, delta) at rest, and the Taylor series of Eqs.
+    pressure_relief_valve_1-3 about that point, with s = t - t_lift, is
+      y1 = beta q s^3/6 - kappa beta q s^4/24 + beta q (kappa^2 - 1) s^5/120
+           + (beta q (2 kappa - kappa^3) - beta^2 q sqrt(delta)) s^6/720 + O(s^7),
+      y3 = delta + beta q s - beta^2 q sqrt(delta) s^4/24 + O(s^5).
+    A lift time off by d moves y1(s) by about 3 d / s relative, so the
+    2e-7 bound below catches d > 1e-9; a wrong sign or rate in the closed
+    form fails outright.  (The short motion before the valve sticks, with
+    y1 slightly below zero, raises y3 by 4.7e-9 more than beta q t, so the
+    lift comes 2.3e-10 early: 1.4e-7 of y1 at s = 0.005.)"""
+    q, kappa, delta, beta, rr = 1.0, 1.25, 10.0, 20.0, 0.8
+    P = _prv_params(q)
+    y30 = 5.0
+    t_lift = (delta - y30) / (beta * q)
+    for t1 in (0.1, t_lift - 1e-3):
+        tol = oracle.make_tol(rtol=1e-10, atol=1e-10, dt0=1e-3, dt_min=1e-14, dt_max=1.0, event_tol=1e-6,
+                              t0=0.0, t1=t1, acc_t_start=0.0)
+        r = oracle.cashkarp_solve(oracle.PRV, P, [[0.0], [0.0], [y30]], tol)
+        assert r["status"][0] == 0 and r["t"][0] == t1
+        assert r["y"][0, 0] == 0.0 and r["y"][1, 0] == 0.0
+        assert int(r["acc"][34, 0]) == 1                     # the one impact that made it stick
+        # the impact took about 5e-4 of time with |y1| < 1e-6, so y3 followed beta q
+        # to within beta * 1e-6 * sqrt(delta) * 5e-4 < 1e-7
+        assert abs(r["y"][2, 0] - (y30 + beta * q * t1)) < 1e-7
+    for s in (0.005, 0.01, 0.02):
+        tol = oracle.make_tol(rtol=1e-12, atol=1e-12, dt0=1e-3, dt_min=1e-14, dt_max=1.0, event_tol=1e-6,
+                              t0=0.0, t1=t_lift + s, acc_t_start=0.0)
+        r = oracle.cashkarp_solve(oracle.PRV, P, [[0.0], [0.0], [y30]], tol)
+        assert r["status"][0] == 0
+        bq = beta * q
+        y1 = (bq * s ** 3 / 6 - kappa * bq * s ** 4 / 24 + bq * (kappa ** 2 - 1) * s ** 5 / 120
+              + (bq * (2 * kappa - kappa ** 3) - beta ** 2 * q * math.sqrt(delta)) * s ** 6 / 720)
+        y3 = delta + bq * s - beta ** 2 * q * math.sqrt(delta) * s ** 4 / 24
+        assert abs(r["y"][0, 0] / y1 - 1.0) < 2e-7, (s, r["y"][0, 0], y1)
+        assert abs(r["y"][2, 0] - y3) < 1e-8 * delta, (s, r["y"][2, 0], y3)
+        assert int(r["acc"][34, 0]) == 1
 
 
 def test_prv_impacts_keep_body_on_or_above_seat():
