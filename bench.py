@@ -67,9 +67,7 @@ def _dist():
 def km_slice(world: int, rank: int, m: int = 362, n_phases: int = 64):
     """Rank `rank`'s share of a (m world) x m grid: every world-th p_A row."""
     full = W.km(m * world, m, n_phases=n_phases)
-    rows = np.arange(rank, m * world, world)
-    idx = (rows[:, None] * m + np.arange(m)[None, :]).ravel()
-    return W.take(full, idx)
+    return W.take(full, W.shard_rows(m * world, m, world, rank))
 
 
 # ---------------------------------------------------------------------------

@@ -423,9 +423,13 @@ ens_status ens_eval_rhs(ens_system sys, int64_t n, const double *params, const d
  * different streams, or from different host threads) race on it.  No call
  * to cudaMalloc, cudaFree or any allocating routine is made.  Work is
  * enqueued on `stream` (one small synchronous read selects the
- * Keller-Miksis kernel variant).  Returns ENS_OK, ENS_EINVAL (arguments, n
- * above the cap, non-device arrays), ENS_ENOTSUP (other systems or
- * precisions) or ENS_ECUDA. */
+ * Keller-Miksis kernel variant).  The solver settings are validated as
+ * ens_create validates them.  Every array must be device memory of the
+ * current device, or managed memory; device memory of another GPU is
+ * refused, since the kernel would reach it as a peer address.  Returns
+ * ENS_OK, ENS_EINVAL (arguments, n above the cap, arrays that are not
+ * addressable as above), ENS_ENOTSUP (other systems or precisions) or
+ * ENS_ECUDA. */
 ens_status ens_solve_noalloc(ens_system sys, int64_t n, const double *params, const double *y0,
                              const double t_span[2], const ens_tol *tol, double *y, double *t_out,
                              double *dt_out, double *acc, int32_t *status, int64_t *nacc, int64_t *nrej,

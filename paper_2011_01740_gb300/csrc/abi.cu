@@ -154,86 +154,14 @@ cudaError_t record_kernel_event(ens_ctx* c, int which, cudaStream_t s) {
                                              : cudaEventRecord(c->kev[which], s);
 }
 
-// Keller-Miksis kernel selection: bit kKmDual if any system drives with a
-// second frequency (C6 or C8 != 0), bit kKmGeneralExponent if any C10 is not
-// within 4 ulp of 21/5 (then pow() is used instead of the fifth-root form).
-__global__ void km_flags_kernel(const double* C, int64_t n, unsigned* flags) {
-  const double lo = 4.2 - 4 * 8.881784197001252e-16, hi = 4.2 + 4 * 8.881784197001252e-16;
-  unsigned f = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (C[6 * n + i] != 0.0 || C[8 * n + i] != 0.0) f |= kKmDual;
-    const double e = C[10 * n + i];
-    if (!(e >= lo && e <= hi)) f |= kKmGeneralExponent;
-  }
-  if (f) atomicOr(flags, f);
-}
-
 ens_status detect_flags(ens_ctx* c) {
   c->km_flags = 0;
   if (!is_km(c->sys) || c->n == 0) return ENS_OK;
   ENS_CUDA(c, cudaMemset(&c->scratch->any_status, 0, sizeof(unsigned)));
-  const int64_t blocks = std::min<int64_t>((c->n + 255) / 256, 4096);
-  km_flags_kernel<<<(unsigned)blocks, 256>>>(c->params, c->n, &c->scratch->any_status);
-  ENS_CUDA(c, cudaGetLastError());
+  ENS_CUDA(c, launch_km_flags(c->params, c->n, &c->scratch->any_status, 0));
   unsigned flag = 0;
   ENS_CUDA(c, cudaMemcpy(&flag, &c->scratch->any_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
   c->km_flags = flag;
-  return ENS_OK;
-}
-
-ens_status check_tol(ens_ctx* c, ens_solver solver, ens_system sys, const ens_tol& t) {
-  if (solver == ENS_RK4) {
-    if (!(t.dt0 > 0.0) || t.n_steps < 0) {
-      set_err(c, "RK4 needs dt0 > 0 and n_steps >= 0");
-      return ENS_EINVAL;
-    }
-    if (sys != ENS_SYS_TOY_X2P && sys != ENS_SYS_LORENZ) {
-      set_err(c, "RK4 runs the smooth systems (x2p, Lorenz); the relief valve needs event "
-                 "handling and Keller-Miksis needs step control");
-      return ENS_ENOTSUP;
-    }
-    if (t.prec != ENS_FP64 && t.prec != ENS_FP64_STRICT) {
-      set_err(c, "RK4 supports ENS_FP64 and ENS_FP64_STRICT");
-      return ENS_ENOTSUP;
-    }
-    return ENS_OK;
-  }
-  if (!(t.rtol >= 0.0) || !(t.atol >= 0.0) || !(t.rtol > 0.0 || t.atol > 0.0) || !(t.dt0 > 0.0) ||
-      !(t.dt_min > 0.0) || !(t.dt_max >= t.dt_min) || t.max_steps <= 0 || t.n_phases < 0) {
-    set_err(c, "adaptive solve needs rtol, atol >= 0 (not both 0), 0 < dt_min <= dt_max, dt0 > 0, "
-               "max_steps > 0, n_phases >= 0");
-    return ENS_EINVAL;
-  }
-  if (t.n_phases > 0 && !(t.phase_len > 0.0)) {
-    set_err(c, "phase mode needs phase_len > 0");
-    return ENS_EINVAL;
-  }
-  if (t.n_transient < 0 || (t.n_phases > 0 ? t.n_transient >= t.n_phases : t.n_transient != 0)) {
-    set_err(c, "n_transient must satisfy 0 <= n_transient < n_phases (0 outside phase mode)");
-    return ENS_EINVAL;
-  }
-  if (sys == ENS_SYS_RELIEF_VALVE && !(t.event_tol > 0.0)) {
-    set_err(c, "the relief valve needs event_tol > 0");
-    return ENS_EINVAL;
-  }
-  if (sys == ENS_SYS_KELLER_MIKSIS_TANGENT && !(t.n_phases > 0 && t.prec == ENS_FP64)) {
-    set_err(c, "the tangent system runs in phase mode (n_phases > 0) in FP64");
-    return ENS_ENOTSUP;
-  }
-  if (sys == ENS_SYS_RELIEF_VALVE && t.n_phases > 0) {
-    set_err(c, "the relief valve runs in event mode (n_phases must be 0)");
-    return ENS_ENOTSUP;
-  }
-  if ((t.prec == ENS_FP32_COMP || t.prec == ENS_FP32X2) &&
-      !(sys == ENS_SYS_KELLER_MIKSIS && t.n_phases > 0 && solver == ENS_RKCK45)) {
-    set_err(c, "ENS_FP32_COMP and ENS_FP32X2 are implemented for the Keller-Miksis phase mode with Cash-Karp");
-    return ENS_ENOTSUP;
-  }
-  if (t.prec != ENS_FP64 && t.prec != ENS_FP32_COMP && t.prec != ENS_FP32X2) {
-    set_err(c, "adaptive solves support ENS_FP64, ENS_FP32_COMP and ENS_FP32X2");
-    return ENS_ENOTSUP;
-  }
   return ENS_OK;
 }
 
@@ -300,7 +228,6 @@ AdaptLaunch adapt_launch(const ens_ctx* c, const ens_launch& L) {
 
 // Enqueue one solve (no graph).  `L` is the launch to use; `shorten` > 0 runs
 // a reduced problem for tuning and planning (phases / horizon / steps cut).
-constexpr double kPilotTol = 1e-7;  // loosest tolerance of the claim-order pilot
 
 ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int shorten) {
   ENS_CUDA(c, cudaMemsetAsync(c->scratch, 0, sizeof(Scratch), s));
@@ -374,6 +301,84 @@ std::mutex g_tune_mu;
 namespace ens {
 // Message of a failed call that has no context, returned by ens_last_error(NULL).
 void set_call_error(const char* msg) { set_err(nullptr, "%s", msg); }
+
+// Keller-Miksis kernel selection: bit kKmDual if any system drives with a
+// second frequency (C6 or C8 != 0), bit kKmGeneralExponent if any C10 is not
+// within 4 ulp of 21/5 (then pow() is used instead of the fifth-root form).
+__global__ void km_flags_kernel(const double* C, int64_t n, unsigned* flags) {
+  const double lo = 4.2 - 4 * 8.881784197001252e-16, hi = 4.2 + 4 * 8.881784197001252e-16;
+  unsigned f = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (C[6 * n + i] != 0.0 || C[8 * n + i] != 0.0) f |= kKmDual;
+    const double e = C[10 * n + i];
+    if (!(e >= lo && e <= hi)) f |= kKmGeneralExponent;
+  }
+  if (f) atomicOr(flags, f);
+}
+
+cudaError_t launch_km_flags(const double* C, int64_t n, unsigned* flags, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  km_flags_kernel<<<(unsigned)blocks, 256, 0, s>>>(C, n, flags);
+  return cudaGetLastError();
+}
+
+ens_status check_tol(ens_ctx* c, ens_solver solver, ens_system sys, const ens_tol& t) {
+  if (solver == ENS_RK4) {
+    if (!(t.dt0 > 0.0) || t.n_steps < 0) {
+      set_err(c, "RK4 needs dt0 > 0 and n_steps >= 0");
+      return ENS_EINVAL;
+    }
+    if (sys != ENS_SYS_TOY_X2P && sys != ENS_SYS_LORENZ) {
+      set_err(c, "RK4 runs the smooth systems (x2p, Lorenz); the relief valve needs event "
+                 "handling and Keller-Miksis needs step control");
+      return ENS_ENOTSUP;
+    }
+    if (t.prec != ENS_FP64 && t.prec != ENS_FP64_STRICT) {
+      set_err(c, "RK4 supports ENS_FP64 and ENS_FP64_STRICT");
+      return ENS_ENOTSUP;
+    }
+    return ENS_OK;
+  }
+  if (!(t.rtol >= 0.0) || !(t.atol >= 0.0) || !(t.rtol > 0.0 || t.atol > 0.0) || !(t.dt0 > 0.0) ||
+      !(t.dt_min > 0.0) || !(t.dt_max >= t.dt_min) || t.max_steps <= 0 || t.n_phases < 0) {
+    set_err(c, "adaptive solve needs rtol, atol >= 0 (not both 0), 0 < dt_min <= dt_max, dt0 > 0, "
+               "max_steps > 0, n_phases >= 0");
+    return ENS_EINVAL;
+  }
+  if (t.n_phases > 0 && !(t.phase_len > 0.0)) {
+    set_err(c, "phase mode needs phase_len > 0");
+    return ENS_EINVAL;
+  }
+  if (t.n_transient < 0 || (t.n_phases > 0 ? t.n_transient >= t.n_phases : t.n_transient != 0)) {
+    set_err(c, "n_transient must satisfy 0 <= n_transient < n_phases (0 outside phase mode)");
+    return ENS_EINVAL;
+  }
+  if (sys == ENS_SYS_RELIEF_VALVE && !(t.event_tol > 0.0)) {
+    set_err(c, "the relief valve needs event_tol > 0");
+    return ENS_EINVAL;
+  }
+  if (sys == ENS_SYS_KELLER_MIKSIS_TANGENT && !(t.n_phases > 0 && t.prec == ENS_FP64)) {
+    set_err(c, "the tangent system runs in phase mode (n_phases > 0) in FP64");
+    return ENS_ENOTSUP;
+  }
+  if (sys == ENS_SYS_RELIEF_VALVE && t.n_phases > 0) {
+    set_err(c, "the relief valve runs in event mode (n_phases must be 0)");
+    return ENS_ENOTSUP;
+  }
+  if ((t.prec == ENS_FP32_COMP || t.prec == ENS_FP32X2) &&
+      !(sys == ENS_SYS_KELLER_MIKSIS && t.n_phases > 0 && solver == ENS_RKCK45)) {
+    set_err(c, "ENS_FP32_COMP and ENS_FP32X2 are implemented for the Keller-Miksis phase mode with Cash-Karp");
+    return ENS_ENOTSUP;
+  }
+  if (t.prec != ENS_FP64 && t.prec != ENS_FP32_COMP && t.prec != ENS_FP32X2) {
+    set_err(c, "adaptive solves support ENS_FP64, ENS_FP32_COMP and ENS_FP32X2");
+    return ENS_ENOTSUP;
+  }
+  return ENS_OK;
+}
+
 }  // namespace ens
 
 namespace {
@@ -712,9 +717,8 @@ ens_status ens_eval_rhs(ens_system sys, int64_t n, const double* params, const d
     unsigned* f = nullptr;
     if (cudaMalloc(&f, sizeof(unsigned)) != cudaSuccess) return ENS_ENOMEM;
     cudaMemsetAsync(f, 0, sizeof(unsigned), s);
-    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
-    km_flags_kernel<<<(unsigned)blocks, 256, 0, s>>>(params, n, f);
-    cudaError_t e = cudaMemcpyAsync(&flags, f, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = launch_km_flags(params, n, f, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, f, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(f);
     if (e != cudaSuccess) return ENS_ECUDA;

@@ -158,4 +158,17 @@ constexpr double e1 = b1 - 5179.0 / 57600.0, e3 = b3 - 7571.0 / 16695.0, e4 = b4
 // Embedded Runge-Kutta pair of the adaptive kernels.
 enum Pair : int { kCashKarp = 0, kDormandPrince = 1 };
 
+// Loosest tolerance of the claim-order pilot.  The pilot only ranks systems by
+// their step counts, so it runs at max(tol, 1e-7): a quarter of the steps of a
+// 1e-10 pilot, and the claim order never changes what a system computes.
+constexpr double kPilotTol = 1e-7;
+
+// Host helpers of abi.cu shared with the other entry points.
+// Validates the solver settings of an adaptive or fixed-step solve; on failure
+// writes the message to ctx (or, for ctx == nullptr, to ens_last_error(NULL)).
+ens_status check_tol(ens_ctx* ctx, ens_solver solver, ens_system sys, const ens_tol& t);
+// ORs the Keller-Miksis kernel-selection flags (kKmDual, kKmGeneralExponent)
+// of n systems' coefficients C [13][n] into *flags (device memory), on s.
+cudaError_t launch_km_flags(const double* C, int64_t n, unsigned* flags, cudaStream_t s);
+
 }  // namespace ens

@@ -63,29 +63,25 @@ cudaError_t scratch_for_device(int dev, unsigned char** ptr, int* sms) {
   return cudaSuccess;
 }
 
-// Keller-Miksis kernel selection (second frequency; exponent 21/5).
-__global__ void noalloc_km_flags_kernel(const double* C, int64_t n, unsigned* flags) {
-  const double lo = 4.2 - 4 * 8.881784197001252e-16, hi = 4.2 + 4 * 8.881784197001252e-16;
-  unsigned f = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (C[6 * n + i] != 0.0 || C[8 * n + i] != 0.0) f |= kKmDual;
-    const double e = C[10 * n + i];
-    if (!(e >= lo && e <= hi)) f |= kKmGeneralExponent;
-  }
-  if (f) atomicOr(flags, f);
-}
-
 ens_status fail(ens_status st, const char* msg) {
   set_call_error(msg);
   return st;
 }
 
-bool on_device(const void* p) {
+// Whether p is memory that a kernel on device `dev` may address directly:
+// device memory of that device, or managed memory.  Device memory of another
+// GPU is refused: the kernel would reach it as a peer address, which faults
+// unless peer access is enabled.  cudaGetLastError clears only the error a
+// failed attribute query of this call left, not one of the caller's.
+bool on_device(const void* p, int dev) {
   if (!p) return false;
   cudaPointerAttributes at{};
-  const bool ok = cudaPointerGetAttributes(&at, p) == cudaSuccess;
-  cudaGetLastError();
-  return ok && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -102,18 +98,21 @@ extern "C" ens_status ens_solve_noalloc(ens_system sys, int64_t n, const double*
   if (tol->prec != ENS_FP64) return fail(ENS_ENOTSUP, "ens_solve_noalloc: FP64 only");
   if ((sys == ENS_SYS_KELLER_MIKSIS) != (tol->n_phases > 0))
     return fail(ENS_EINVAL, "ens_solve_noalloc: Keller-Miksis needs n_phases > 0, the relief valve n_phases = 0");
-  if (!(tol->rtol > 0.0 || tol->atol > 0.0) || !(tol->dt0 > 0.0) || !(tol->dt_min > 0.0) ||
-      !(tol->dt_max >= tol->dt_min) || tol->max_steps <= 0 ||
-      (sys == ENS_SYS_RELIEF_VALVE && !(tol->event_tol > 0.0 && t_span[1] > t_span[0])) ||
-      (sys == ENS_SYS_KELLER_MIKSIS && !(tol->phase_len > 0.0)) || tol->n_transient < 0 ||
-      (sys == ENS_SYS_KELLER_MIKSIS ? tol->n_transient >= tol->n_phases : tol->n_transient != 0))
-    return fail(ENS_EINVAL, "ens_solve_noalloc: invalid tolerances or time span");
+  // the same validation as ens_create (tolerances, steps, phases, event band)
+  const ens_status tst = check_tol(nullptr, ENS_RKCK45, sys, *tol);
+  if (tst != ENS_OK) return tst;
+  if (sys == ENS_SYS_RELIEF_VALVE && !(t_span[1] > t_span[0]))
+    return fail(ENS_EINVAL, "ens_solve_noalloc: t_span[1] must exceed t_span[0]");
   if (n == 0) return ENS_OK;
-  if (!on_device(params) || !on_device(y0) || !on_device(y) || !on_device(t_out) || !on_device(dt_out) ||
-      !on_device(acc) || !on_device(status) || !on_device(nacc) || !on_device(nrej) || !on_device(nrhs))
-    return fail(ENS_EINVAL, "ens_solve_noalloc: every array must be device memory");
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return fail(ENS_ECUDA, "ens_solve_noalloc: no current device");
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ENS_ECUDA, "ens_solve_noalloc: no current device");
+  }
+  const void* arrays[] = {params, y0, y, t_out, dt_out, acc, status, nacc, nrej, nrhs};
+  for (const void* p : arrays)
+    if (!on_device(p, dev))
+      return fail(ENS_EINVAL, "ens_solve_noalloc: every array must be device (or managed) memory of the current device");
   unsigned char* base = nullptr;
   int sms = 0;
   if (scratch_for_device(dev, &base, &sms) != cudaSuccess)
@@ -128,9 +127,8 @@ extern "C" ens_status ens_solve_noalloc(ens_system sys, int64_t n, const double*
   if (sys == ENS_SYS_KELLER_MIKSIS) {
     if (cudaMemsetAsync(flags_d, 0, sizeof(unsigned), s) != cudaSuccess)
       return fail(ENS_ECUDA, "ens_solve_noalloc: clearing the scratch failed");
-    const int64_t blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
-    noalloc_km_flags_kernel<<<(unsigned)blocks, 256, 0, s>>>(params, n, flags_d);
-    if (cudaMemcpyAsync(&flags, flags_d, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (launch_km_flags(params, n, flags_d, s) != cudaSuccess ||
+        cudaMemcpyAsync(&flags, flags_d, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return fail(ENS_ECUDA, "ens_solve_noalloc: kernel selection failed");
   }
@@ -171,6 +169,8 @@ extern "C" ens_status ens_solve_noalloc(ens_system sys, int64_t n, const double*
     p.persistent = 0;
     if (p.n_phases > 0) p.n_phases = 1;
     else p.t1 = p.t0 + (p.t1 - p.t0) / 16.0;
+    p.rtol = p.rtol > kPilotTol ? p.rtol : kPilotTol;
+    p.atol = p.atol > kPilotTol ? p.atol : kPilotTol;
     if (launch_ck45(sys, flags, p, AdaptLaunch{(n + 127) / 128, 128}, s) != cudaSuccess ||
         launch_order(nacc, n, order, hist, s) != cudaSuccess ||
         cudaMemsetAsync(scr, 0, sizeof(Scratch), s) != cudaSuccess)

@@ -277,7 +277,9 @@ struct KellerMiksis {
 // Pressure relief valve (Sec. 4.3, Eqs. pressure_relief_valve_1-3):
 //   y1' = y2, y2' = -kappa y2 - (y1 + delta) + y3, y3' = beta (q - y1 sqrt(y3)).
 // sqrt is taken of max(y3, 0): y3 >= 0 for q > 0, the clamp only keeps a
-// rounding excursion from producing a NaN; it is sqrt_nr (about 2 ulp).
+// rounding excursion from producing a NaN; it is sqrt_nr (about 2 ulp).  The
+// clamp tests the sign bit on the integer pipe (negative values and -0 give
+// +0), which spares the FP64 pipe a min / max per evaluation.
 // ---------------------------------------------------------------------------
 struct ReliefValve {
   static constexpr int kDim = 3;
@@ -295,7 +297,8 @@ struct ReliefValve {
     (void)t;
     dy[0] = y[1];
     dy[1] = fma(-kappa, y[1], y[2] - (y[0] + delta));
-    dy[2] = beta * fma(-y[0], sqrt_nr(fmax(y[2], 0.0)), q);
+    const double y3 = __double2hiint(y[2]) < 0 ? 0.0 : y[2];
+    dy[2] = beta * fma(-y[0], sqrt_nr(y3), q);
   }
   using Drive = NoDrive;
   __device__ __forceinline__ Drive drive(double) const { return {}; }

@@ -144,32 +144,62 @@ __device__ __forceinline__ void pair_trial(const Sys& s, double t, double h, con
 // right-hand-side evaluations of one trial besides k1
 constexpr uint32_t pair_rhs(int PAIR) { return PAIR == kDormandPrince ? 6u : 5u; }
 
+// Compares, max / min and clamps of doubles on the integer pipe.  On this
+// part the FP64 pipe carries every flop of the solver and is the bottleneck; a
+// compare or a min / max costs it a full FP64 issue slot, the same as an FMA.
+// For x >= +0 (with +inf, and NaN with its sign bit clear, above every finite
+// value) the IEEE bit pattern read as a signed 64-bit integer orders exactly
+// as the value does, so these need no FP64 instruction.  For doubles of
+// either sign, okey() flips the magnitude bits of negatives, which orders all
+// finite values (with -0 just below +0).
+__device__ __forceinline__ long long nnbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double absd(double x) {
+  return __hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x));
+}
+// a, b >= +0 or NaN (sign clear): NaN dominates max
+__device__ __forceinline__ double nnmax(double a, double b) { return nnbits(a) >= nnbits(b) ? a : b; }
+__device__ __forceinline__ double nnmin(double a, double b) { return nnbits(a) <= nnbits(b) ? a : b; }
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+// the larger / smaller of two finite doubles, keeping `a` on ties (as
+// `if (b > a) a = b` does)
+__device__ __forceinline__ double omax(double a, double b) { return okey(b) > okey(a) ? b : a; }
+__device__ __forceinline__ double omin(double a, double b) { return okey(b) < okey(a) ? b : a; }
+
+// E = max_c |err_c| / (atol + rtol max(|y_c|, |y5_c|)), >= 0, or NaN (sign
+// clear) when a trial blew up.  rcp_nr is within 1 ulp of 1/sc for the
+// normal, finite sc of a solve; a zero, subnormal, infinite or NaN sc gives
+// NaN, and a NaN stays the maximum.
 template <int D>
 __device__ __forceinline__ double err_norm(const double* y, const double* y5, const double* err,
                                            double rtol, double atol) {
   double E = 0.0;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    const double sc = fma(rtol, fmax(fabs(y[c]), fabs(y5[c])), atol);
-    // rcp_nr is within 1 ulp of 1/sc for the normal, finite sc of a solve; a
-    // zero, subnormal or infinite sc (blown-up trial) gives NaN: rejected
-    const double r = fabs(err[c]) * rcp_nr(sc);
-    if (isnan(r)) E = r;
-    else if (r > E) E = r;   // E stays NaN once NaN: NaN > r comparisons are false
+    const double sc = fma(rtol, nnmax(absd(y[c]), absd(y5[c])), atol);
+    const double r = absd(absd(err[c]) * rcp_nr(sc));
+    E = nnmax(E, r);
   }
   return E;
 }
+// accept iff E <= 1 (false for NaN)
+__device__ __forceinline__ bool accept(double E) { return nnbits(E) <= nnbits(1.0); }
 
 // fac = clamp(0.9 E^(-1/5), 0.2, 5).  0.9 E^(-1/5) leaves [0.2, 5] for
 // E > 4.5^5 = 1845.3 and E < 0.18^5 = 1.9e-4, so E is clamped to [1e-4, 2000]
 // first (same result, and keeps inv_fifth_root inside the float range).
+// E >= 0 or NaN as err_norm returns it.
 __device__ __forceinline__ double step_factor(double E) {
-  if (isnan(E)) return 0.2;
-  const double Ec = E < 1e-4 ? 1e-4 : (E > 2000.0 ? 2000.0 : E);
-  double fac = 0.9 * inv_fifth_root(Ec);
-  fac = fac < 0.2 ? 0.2 : fac;
-  fac = fac > 5.0 ? 5.0 : fac;
-  return fac;
+  if (nnbits(E) > nnbits(__longlong_as_double(0x7ff0000000000000LL))) return 0.2;  // NaN
+  const double Ec = nnmin(nnmax(E, 1e-4), 2000.0);
+  const double fac = 0.9 * inv_fifth_root(Ec);
+  return nnmin(nnmax(fac, 0.2), 5.0);
+}
+// the next step proposal after an accepted trial, within [dt_min, dt_max]
+__device__ __forceinline__ double bounded_step(double h, double fac, double dt_min, double dt_max) {
+  return nnmax(nnmin(h * fac, dt_max), dt_min);
 }
 
 // Claim the next system of a persistent lane (or the lane's own system in
@@ -268,8 +298,9 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
     } else {
       double h = dt;
       bool clamped = false;
-      if (h >= tau_end - tau) {
-        h = tau_end - tau;
+      const double rest = tau_end - tau;  // > 0 inside a phase
+      if (nnbits(h) >= nnbits(rest)) {
+        h = rest;
         clamped = true;
       }
       if (!k1v) {
@@ -282,7 +313,7 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
       ++trials;
       const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
       const double fac = step_factor(E);
-      if (E <= 1.0) {
+      if (accept(E)) {
         tau = clamped ? tau_end : tau + h;
         dk = d5;  // drive at tau + h; a phase end below resets it
 #pragma unroll
@@ -292,14 +323,10 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
         }
         k1v = PAIR == kDormandPrince;  // k7 = f(tau + h, y5); a phase end below clears it
         ++nacc;
-        ymax = fmax(ymax, y[0]);
-        ymin = fmin(ymin, y[0]);
-        if (!clamped) {
-          dt = h * fac;
-          dt = dt > a.dt_max ? a.dt_max : dt;
-          dt = dt < a.dt_min ? a.dt_min : dt;
-        }
-        if (!(tau < tau_end)) {
+        ymax = omax(ymax, y[0]);
+        ymin = omin(ymin, y[0]);
+        if (!clamped) dt = bounded_step(h, fac, a.dt_min, a.dt_max);
+        if (okey(tau) >= okey(tau_end)) {  // !(tau < tau_end): tau + h may round onto the end
           if (ph >= a.n_transient) {
             a.acc[(int64_t)(2 * (ph - a.n_transient)) * a.n + i] = ymax;
             a.acc[(int64_t)(2 * (ph - a.n_transient) + 1) * a.n + i] = ymin;
@@ -322,7 +349,7 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
       } else {
         ++nrej;
         dt = h * fac;
-        if (dt < a.dt_min) st |= kStDtUnderflow;  // retired at the next iteration
+        if (nnbits(dt) < nnbits(a.dt_min)) st |= kStDtUnderflow;  // retired at the next iteration
       }
     }
     if (sys_done) {
@@ -439,16 +466,17 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
         stuck = false;
       }
       k1v = false;
-      if (t >= a.acc_t_start && y[0] < ymin) ymin = y[0];
-      if (!(t < a.t1)) sys_done = true;
+      if (okey(t) >= okey(a.acc_t_start) && okey(y[0]) < okey(ymin)) ymin = y[0];
+      if (okey(t) >= okey(a.t1)) sys_done = true;
     } else {
       double h = dt;
       int limited = 0;
-      if (h >= a.t1 - t) {
-        h = a.t1 - t;
+      const double rest = a.t1 - t;  // > 0 before the end
+      if (nnbits(h) >= nnbits(rest)) {
+        h = rest;
         limited = 1;
       }
-      if (h_ev > 0.0 && h_ev < h) {
+      if (nnbits(h_ev) > 0 && nnbits(h_ev) < nnbits(h)) {  // h_ev >= 0
         h = h_ev;
         limited = 2;
       }
@@ -462,22 +490,24 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
       ++trials;
       const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
       const double fac = step_factor(E);
-      if (!(E <= 1.0)) {
+      if (!accept(E)) {
         ++nrej;
         dt = h * fac;
         h_ev = 0.0;
-        if (dt < a.dt_min) st |= kStDtUnderflow;
+        if (nnbits(dt) < nnbits(a.dt_min)) st |= kStDtUnderflow;
       } else {
+        // y and y5 are finite here (a non-finite trial has E = NaN and is rejected)
+        const long long kt = okey(etol), knt = okey(-etol);
         double best = 2.0;
         bool overshoot = false;
-        if (y5[0] < -etol) {  // impact beyond the band
-          const double frac = (y[0] > etol) ? event_frac(y[0], k1[0], y5[0], h) : 0.5;
-          best = frac < best ? frac : best;
+        if (okey(y5[0]) < knt) {  // impact beyond the band
+          const double frac = (okey(y[0]) > kt) ? event_frac(y[0], k1[0], y5[0], h) : 0.5;
+          best = nnmin(frac, best);
           overshoot = true;
         }
-        if (y[1] > etol && y5[1] < -etol) {  // maximum beyond the band
+        if (okey(y[1]) > kt && okey(y5[1]) < knt) {  // maximum beyond the band
           const double frac = event_frac(y[1], k1[1], y5[1], h);
-          best = frac < best ? frac : best;
+          best = nnmin(frac, best);
           overshoot = true;
         }
         if (overshoot) {
@@ -495,16 +525,13 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
           ++nacc;
           ev_retries = 0;
           h_ev = 0.0;
-          if (!limited) {
-            dt = h * fac;
-            dt = dt > a.dt_max ? a.dt_max : dt;
-            dt = dt < a.dt_min ? a.dt_min : dt;
-          }
-          if (y1_old > etol && fabs(y[1]) <= etol) {  // Poincare point
+          if (!limited) dt = bounded_step(h, fac, a.dt_min, a.dt_max);
+          if (okey(y1_old) > kt && nnbits(absd(y[1])) <= nnbits(etol)) {  // Poincare point
             a.acc[(int64_t)(nmax % kRing) * a.n + i] = y[0];
             ++nmax;
           }
-          if (fabs(y[0]) <= etol && y[1] < 0.0) {  // impact law
+          // impact law when |y1| <= tol and y2 < 0 (okey(-0.0) = -1: -0 is not below zero)
+          if (nnbits(absd(y[0])) <= nnbits(etol) && okey(y[1]) < -1LL) {
             y[0] = 0.0;
             y[1] = -s.r * y[1];
             k1v = false;
@@ -515,8 +542,8 @@ __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
               stuck = true;
             }
           }
-          if (t >= a.acc_t_start && y[0] < ymin) ymin = y[0];
-          if (!(t < a.t1)) sys_done = true;
+          if (okey(t) >= okey(a.acc_t_start) && okey(y[0]) < okey(ymin)) ymin = y[0];
+          if (okey(t) >= okey(a.t1)) sys_done = true;
         }
       }
     }
@@ -579,8 +606,9 @@ __global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
     } else {
       double h = dt;
       bool clamped = false;
-      if (h >= a.t1 - t) {
-        h = a.t1 - t;
+      const double rest = a.t1 - t;  // > 0 before the end
+      if (nnbits(h) >= nnbits(rest)) {
+        h = rest;
         clamped = true;
       }
       if (!k1v) {
@@ -593,7 +621,7 @@ __global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
       ++trials;
       const double E = err_norm<D>(y, y5, err, a.rtol, a.atol);
       const double fac = step_factor(E);
-      if (E <= 1.0) {
+      if (accept(E)) {
         t = clamped ? a.t1 : t + h;
         dk = d5;  // t + h; a clamped step ends the system
 #pragma unroll
@@ -603,16 +631,12 @@ __global__ void __launch_bounds__(256) ck_plain_kernel(AdaptArgs a) {
         }
         k1v = PAIR == kDormandPrince;
         ++nacc;
-        if (!clamped) {
-          dt = h * fac;
-          dt = dt > a.dt_max ? a.dt_max : dt;
-          dt = dt < a.dt_min ? a.dt_min : dt;
-        }
-        if (!(t < a.t1)) sys_done = true;
+        if (!clamped) dt = bounded_step(h, fac, a.dt_min, a.dt_max);
+        if (okey(t) >= okey(a.t1)) sys_done = true;
       } else {
         ++nrej;
         dt = h * fac;
-        if (dt < a.dt_min) st |= kStDtUnderflow;
+        if (nnbits(dt) < nnbits(a.dt_min)) st |= kStDtUnderflow;
       }
     }
     if (sys_done) {

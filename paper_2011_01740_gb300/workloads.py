@@ -185,6 +185,16 @@ def subsample(n: int, k: int, seed: int = SEED, strata: int = 64) -> np.ndarray:
     return np.sort(np.concatenate(out))
 
 
+def shard_rows(m_rows: int, m_cols: int, world: int, rank: int) -> np.ndarray:
+    """Global system indices of rank `rank`'s shard of an m_rows x m_cols grid
+    (row-major, columns fastest): every world-th row, starting at row `rank`.
+    The systems are independent, so shards need no exchange while solving;
+    interleaved rows give every rank the same mix of driving amplitudes, hence
+    about the same cost.  The shards of ranks 0..world-1 partition the grid."""
+    rows = np.arange(rank, m_rows, world)
+    return (rows[:, None] * m_cols + np.arange(m_cols)[None, :]).ravel()
+
+
 def take(d: dict, idx: np.ndarray) -> dict:
     """Restrict a workload's per-system arrays to the systems `idx`."""
     out = dict(d)

@@ -115,3 +115,24 @@ def test_host_planner_matches_oracle_coefficients(ens):
     C = ens.ens_km_coefficients(pA1, f1, pA2, f2, th, RE, W.WATER_25C)
     Co = oracle.km_coefficients(pA1, f1, pA2, f2, th, RE, oracle.liquid(**W.WATER_25C))
     np.testing.assert_allclose(C, Co, rtol=4e-15, atol=0)
+
+
+def test_noalloc_validates_like_create_before_any_device_work(ens):
+    """ens_solve_noalloc applies ens_create's tolerance checks (a negative rtol
+    with a positive atol is refused) and its own cap on n, all before it
+    touches a device."""
+    z = np.zeros(1)
+    outs = [z] * 8
+    bad = ens.make_tol(rtol=-1.0, atol=1e-10, n_phases=2)
+    with pytest.raises(ens.EnsError) as e:
+        ens.ens_solve_noalloc(ens.ENS_SYS_KELLER_MIKSIS, 1, z, z, (0.0, 1.0), bad, *outs)
+    assert e.value.status == ens.ENS_EINVAL
+    assert "rtol" in str(e.value)
+    with pytest.raises(ens.EnsError) as e:
+        ens.ens_solve_noalloc(ens.ENS_SYS_KELLER_MIKSIS, (1 << 20) + 1, z, z, (0.0, 1.0),
+                              ens.make_tol(n_phases=2), *outs)
+    assert e.value.status == ens.ENS_EINVAL and "1048576" in str(e.value)
+    with pytest.raises(ens.EnsError) as e:   # the valve runs in event mode only
+        ens.ens_solve_noalloc(ens.ENS_SYS_RELIEF_VALVE, 1, z, z, (0.0, 1.0),
+                              ens.make_tol(n_phases=2, event_tol=1e-6), *outs)
+    assert e.value.status == ens.ENS_EINVAL

@@ -96,3 +96,21 @@ def test_noalloc_rejects_ensembles_beyond_its_scratch():
                               *[torch.zeros(1, dtype=torch.int64, device="cuda")] * 3)
     assert e.value.status == ens.ENS_EINVAL
     assert "1048576" in str(e.value)
+
+
+def test_noalloc_refuses_host_buffers_before_launching():
+    """Every array must be device memory of the current device (or managed
+    memory); a pageable host array is refused with ENS_EINVAL and no kernel
+    runs on it."""
+    import torch
+    n = 4
+    tol = ens.make_tol(n_phases=1)
+    d = lambda *s, dt=torch.float64: torch.zeros(*s, dtype=dt, device="cuda")
+    host_y0 = np.zeros((2, n))
+    with pytest.raises(ens.EnsError) as e:
+        ens.ens_solve_noalloc(ens.ENS_SYS_KELLER_MIKSIS, n, d(13, n), host_y0, (0.0, 1.0), tol, d(2, n), d(n),
+                              d(n), d(2, n), d(n, dt=torch.int32), d(n, dt=torch.int64), d(n, dt=torch.int64),
+                              d(n, dt=torch.int64))
+    assert e.value.status == ens.ENS_EINVAL
+    assert "current device" in str(e.value)
+    torch.cuda.synchronize()
