@@ -170,7 +170,11 @@ typedef struct {
  *   use_graph      capture the launch sequence of ens_solve in a CUDA graph on
  *                  the first call and replay it afterwards.
  *   cost_order     persistent mode: claim systems in decreasing order of their
- *                  step count in a one-phase pilot solve (longest first). */
+ *                  step count in a one-phase pilot solve (longest first).
+ *   systems_per_thread  RK4: 1, 2 or 4 systems integrated by each thread,
+ *                  their steps interleaved in one instruction stream (0 means
+ *                  1); each system's arithmetic is that of one per thread, so
+ *                  results do not change.  The adaptive solvers take 1. */
 enum { ENS_LAUNCH_PLAIN = 0, ENS_LAUNCH_PERSISTENT = 1 };
 typedef struct {
     int32_t mode;
@@ -178,8 +182,18 @@ typedef struct {
     int32_t blocks_per_sm;
     int32_t use_graph;
     int32_t cost_order;
-    int32_t reserved[3];
+    int32_t systems_per_thread;
+    int32_t reserved[2];
 } ens_launch;
+
+/* One candidate of the last ens_autotune: its launch, the device time in
+ * milliseconds of the main kernel of the shortened solve it was timed on, and
+ * the fraction of the horizon that solve covered. */
+typedef struct {
+    ens_launch launch;
+    double ms;
+    double horizon_frac;
+} ens_tune_row;
 
 /* Liquid and gas constants of the Keller-Miksis model (SI units):
  * density rho_L, sound speed c_L, viscosity mu_L, surface tension sigma,
@@ -259,11 +273,27 @@ int64_t ens_size(const ens_ctx *ctx);
 int32_t ens_dim(const ens_ctx *ctx);
 int32_t ens_npar(const ens_ctx *ctx);
 
-/* Time the candidate launch configurations on this context (plain and
- * persistent, several block sizes and residencies) with short solves on
- * `stream`, keep the fastest, and write it to *best (may be NULL).  The
- * choice is cached per (system, solver, precision, n) for the process. */
+/* Autotuner (the paper tunes block size and registers by hand, Sec. 3.2.2
+ * and Sec. 4.1.2).  Times candidate launches on this context with shortened
+ * solves on `stream`, keeps the fastest as the context's launch (use_graph is
+ * kept) and writes it to *best (may be NULL).
+ *   RK4: block 32..256 x systems_per_thread 1, 2, 4 on 1/8 of the steps.
+ *   Adaptive: persistent launches of 3 to 24 warps per SM with longest-first
+ *   claiming, the best residency without it, and a plain launch, each on
+ *   1/8 of the phases (or of the time span) of every system -- the horizon is
+ *   cut, not the ensemble, so the balance between throughput and the
+ *   longest system's chain stays that of the full solve; the fraction is
+ *   halved while one shortened solve takes over 0.6 s.  The claim order
+ *   comes from the full solve's one-phase pilot, computed once.
+ * The context's outputs hold the last candidate's shortened solve afterwards.
+ * The choice and its table are cached per (system, solver, precision, n,
+ * phases, transient phases, horizon, device) for the process. */
 ens_status ens_autotune(ens_ctx *ctx, void *stream, ens_launch *best);
+
+/* The candidates timed by the context's last ens_autotune, in the order
+ * tried: copies up to `cap` rows into `rows` (may be NULL) and returns how
+ * many there are (0 for a NULL ctx or before any tuning). */
+int32_t ens_autotune_table(const ens_ctx *ctx, ens_tune_row *rows, int32_t cap);
 
 /* Text of the context's last failure ("" if none).  ctx may be NULL: then the
  * last failure of a call that had no context (ens_create) is returned. */
@@ -379,6 +409,30 @@ ens_status ens_km_labels(int64_t n, const double *acc, int32_t n_phases, int32_t
 /* idx[0..*count) = increasing indices i with v[i] > thr (idx holds n
  * entries); *count is written on the host; synchronous. */
 ens_status ens_select_above(int64_t n, const float *v, float thr, int32_t *idx, int64_t *count, void *stream);
+/* The same with two gates: i is selected when v[i] > thr or, if w is not
+ * NULL, w[i] > thr_w (the screening fallback: ensemble spread above its
+ * threshold, or a steep region of the predicted map). */
+ens_status ens_select_gate(int64_t n, const float *v, float thr, const float *w, float thr_w, int32_t *idx,
+                           int64_t *count, void *stream);
+/* Steepness of a map v on a rows x cols grid (row-major, columns fastest)
+ * with feature-space spacings d_row, d_col > 0 between adjacent points:
+ * g = the largest |v(neighbour) - v| / distance over the up to four points
+ * `stride` >= 1 rows or columns away.  Where the predicted map is steep the
+ * training grid resolves the response least, so the screen hands those
+ * points to the solver as well; a stride that keeps the distance near the
+ * training grid's spacing measures the map's slope rather than the
+ * rounding noise of the network's output. */
+ens_status ens_grid_gradient(int64_t rows, int64_t cols, int64_t stride, const float *v, float d_row, float d_col,
+                             float *g, void *stream);
+/* out [5][n][2]: for each feature point x[n][2], the points x, x +- d0 e0,
+ * x +- d1 e1 (e0, e1 the feature axes); with ens_mlp_screen over the 5 n
+ * points and ens_stencil_gradient it gives the grid gradient's steepness at
+ * scattered points (the calibration sample of the screening gate). */
+ens_status ens_feature_stencil(int64_t n, const float *x, float d0, float d1, float *out, void *stream);
+/* g[i] = max(|v[n+i] - v[i]|, |v[2n+i] - v[i]|) / d0 max'ed with
+ * max(|v[3n+i] - v[i]|, |v[4n+i] - v[i]|) / d1, for v [5][n] evaluated at the
+ * points of ens_feature_stencil. */
+ens_status ens_stencil_gradient(int64_t n, const float *v, float d0, float d1, float *g, void *stream);
 /* dst[i] = src[idx[i]] for i < k. */
 ens_status ens_gather_f64(int64_t k, const int32_t *idx, const double *src, double *dst, void *stream);
 /* dst[idx[i]] = y[i][0] for i < k (writes re-solved values into a screened map). */

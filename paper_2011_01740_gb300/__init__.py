@@ -62,11 +62,17 @@ class EnsTol(ctypes.Structure):
 class EnsLaunch(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("cost_order", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("cost_order", ctypes.c_int32), ("systems_per_thread", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self):
         return dict(mode=self.mode, block=self.block, blocks_per_sm=self.blocks_per_sm,
-                    use_graph=self.use_graph, cost_order=self.cost_order)
+                    use_graph=self.use_graph, cost_order=self.cost_order,
+                    systems_per_thread=max(1, self.systems_per_thread))
+
+
+class EnsTuneRow(ctypes.Structure):
+    _fields_ = [("launch", EnsLaunch), ("ms", ctypes.c_double), ("horizon_frac", ctypes.c_double)]
 
 
 class EnsLiquid(ctypes.Structure):
@@ -183,8 +189,8 @@ def make_tol(rtol=1e-10, atol=1e-10, dt0=1e-2, dt_min=1e-14, dt_max=1e-1, event_
 
 
 def make_launch(mode=ENS_LAUNCH_PERSISTENT, block=128, blocks_per_sm=2, use_graph=0,
-                cost_order=0) -> EnsLaunch:
-    return EnsLaunch(mode, block, blocks_per_sm, use_graph, cost_order)
+                cost_order=0, systems_per_thread=1) -> EnsLaunch:
+    return EnsLaunch(mode, block, blocks_per_sm, use_graph, cost_order, systems_per_thread)
 
 
 # ---------------------------------------------------------------------------
@@ -286,6 +292,20 @@ def ens_autotune(ctx: int, stream=None) -> EnsLaunch:
     best = EnsLaunch()
     _check(lib().ens_autotune(ctx, _stream(stream), ctypes.byref(best)), ctx)
     return best
+
+
+def ens_autotune_table(ctx: int) -> list:
+    """Candidates of the context's last ens_autotune: a list of dicts with the
+    launch, the main-kernel milliseconds and the horizon fraction timed."""
+    L = lib()
+    if not getattr(L, "_tune_bound", False):
+        L.ens_autotune_table.argtypes = [ctypes.c_void_p, ctypes.POINTER(EnsTuneRow), ctypes.c_int32]
+        L.ens_autotune_table.restype = ctypes.c_int32
+        L._tune_bound = True
+    n = int(L.ens_autotune_table(ctx, None, 0))
+    rows = (EnsTuneRow * max(n, 1))()
+    n = int(L.ens_autotune_table(ctx, rows, n))
+    return [dict(launch=r.launch.as_dict(), ms=r.ms, horizon_frac=r.horizon_frac) for r in rows[:n]]
 
 
 def ens_eval_rhs(sys: int, n: int, params, t, y, dy, stream=None):
@@ -398,6 +418,16 @@ def _mlp_lib():
         L.ens_km_labels.restype = st
         L.ens_select_above.argtypes = [ctypes.c_int64, vp, ctypes.c_float, vp, ctypes.POINTER(ctypes.c_int64), vp]
         L.ens_select_above.restype = st
+        L.ens_select_gate.argtypes = [ctypes.c_int64, vp, ctypes.c_float, vp, ctypes.c_float, vp,
+                                      ctypes.POINTER(ctypes.c_int64), vp]
+        L.ens_select_gate.restype = st
+        L.ens_grid_gradient.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, ctypes.c_float,
+                                        ctypes.c_float, vp, vp]
+        L.ens_grid_gradient.restype = st
+        L.ens_feature_stencil.argtypes = [ctypes.c_int64, vp, ctypes.c_float, ctypes.c_float, vp, vp]
+        L.ens_feature_stencil.restype = st
+        L.ens_stencil_gradient.argtypes = [ctypes.c_int64, vp, ctypes.c_float, ctypes.c_float, vp, vp]
+        L.ens_stencil_gradient.restype = st
         L.ens_gather_f64.argtypes = [ctypes.c_int64, vp, vp, vp, vp]
         L.ens_gather_f64.restype = st
         L.ens_scatter_labels.argtypes = [ctypes.c_int64, vp, vp, vp, vp]
@@ -512,6 +542,36 @@ def ens_km_labels(n: int, acc, n_phases: int, first_phase: int, spread_tol: floa
     _mcheck(_mlp_lib().ens_km_labels(int(n), _ptr(acc, keep), int(n_phases), int(first_phase), float(spread_tol),
                                      _ptr(y, keep), _stream(stream)))
     return y
+
+
+def ens_select_gate(n: int, v, thr: float, w, thr_w: float, idx, stream=None) -> int:
+    """Indices with v > thr or w > thr_w (w may be None) into idx; returns the count."""
+    keep = []
+    cnt = ctypes.c_int64(0)
+    _mcheck(_mlp_lib().ens_select_gate(int(n), _ptr(v, keep), float(thr), _ptr(w, keep), float(thr_w),
+                                       _ptr(idx, keep), ctypes.byref(cnt), _stream(stream)))
+    return int(cnt.value)
+
+
+def ens_grid_gradient(rows: int, cols: int, stride: int, v, d_row: float, d_col: float, g, stream=None):
+    keep = []
+    _mcheck(_mlp_lib().ens_grid_gradient(int(rows), int(cols), int(stride), _ptr(v, keep), float(d_row),
+                                         float(d_col), _ptr(g, keep), _stream(stream)))
+    return g
+
+
+def ens_feature_stencil(n: int, x, d0: float, d1: float, out, stream=None):
+    keep = []
+    _mcheck(_mlp_lib().ens_feature_stencil(int(n), _ptr(x, keep), float(d0), float(d1), _ptr(out, keep),
+                                           _stream(stream)))
+    return out
+
+
+def ens_stencil_gradient(n: int, v, d0: float, d1: float, g, stream=None):
+    keep = []
+    _mcheck(_mlp_lib().ens_stencil_gradient(int(n), _ptr(v, keep), float(d0), float(d1), _ptr(g, keep),
+                                            _stream(stream)))
+    return g
 
 
 def ens_select_above(n: int, v, thr: float, idx, stream=None) -> int:

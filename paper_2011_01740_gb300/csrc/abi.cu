@@ -14,7 +14,7 @@
 #include "common.cuh"
 
 namespace ens {
-cudaError_t launch_rk4(int sys, bool strict, const Rk4Args& a, int block, cudaStream_t s);
+cudaError_t launch_rk4(int sys, bool strict, const Rk4Args& a, int block, int spt, cudaStream_t s);
 cudaError_t launch_ck45(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_ck45_fp32c(unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_ck45_df(unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
@@ -60,6 +60,10 @@ struct ens_ctx {
   // events around the main solve kernel of the last solve (ens_kernel_ms)
   cudaEvent_t kev[2] = {nullptr, nullptr};
   bool kev_recorded = false;
+  // claim order already in c->order for the tuner's shortened solves
+  bool order_ready = false;
+  // candidates and main-kernel times of the last ens_autotune
+  std::vector<ens_tune_row> tune_rows;
   char err[512] = {0};
 };
 
@@ -107,10 +111,14 @@ ens_launch default_launch(const ens_ctx* c) {
   return L;
 }
 
+int spt_of(const ens_launch& L) { return L.systems_per_thread <= 0 ? 1 : L.systems_per_thread; }
+
 bool valid_launch(const ens_launch& L) {
   if (L.mode != ENS_LAUNCH_PLAIN && L.mode != ENS_LAUNCH_PERSISTENT) return false;
   if (L.block < 32 || L.block > 256 || (L.block % 32) != 0) return false;
   if (L.mode == ENS_LAUNCH_PERSISTENT && (L.blocks_per_sm < 1 || L.blocks_per_sm > 32)) return false;
+  const int spt = spt_of(L);
+  if (spt != 1 && spt != 2 && spt != 4) return false;
   return true;
 }
 
@@ -226,10 +234,43 @@ AdaptLaunch adapt_launch(const ens_ctx* c, const ens_launch& L) {
   return out;
 }
 
-// Enqueue one solve (no graph).  `L` is the launch to use; `shorten` > 0 runs
-// a reduced problem for tuning and planning (phases / horizon / steps cut).
+// The claim order for longest-first scheduling: a pilot of one phase (or 1/16
+// of the horizon) of every system in plain mode, then the systems sorted by
+// decreasing pilot step count into c->order.  The pilot only ranks the
+// systems, so it runs at a tolerance of at least kPilotTol: a quarter of the
+// steps of a 1e-10 pilot, and on the 362 x 362 Keller-Miksis sweep a whole
+// solve 1.4 % faster with the same results (the claim order never changes what
+// a system computes).
+ens_status enqueue_order(ens_ctx* c, const AdaptArgs& a, cudaStream_t s) {
+  AdaptArgs p = a;
+  p.persistent = 0;
+  p.order = nullptr;
+  if (p.n_phases > 0) {
+    p.n_phases = 1;
+    p.n_transient = 0;
+    p.acc_phases = 1;
+  } else {
+    p.t1 = p.t0 + (p.t1 - p.t0) / 16.0;
+  }
+  p.rtol = p.rtol > kPilotTol ? p.rtol : kPilotTol;
+  p.atol = p.atol > kPilotTol ? p.atol : kPilotTol;
+  AdaptLaunch PL{(c->n + 127) / 128, 128};
+  cudaError_t e = launch_adaptive(c, p, PL, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pilot launch");
+  e = launch_order(c->nacc, c->n, c->order, c->hist, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "order launch");
+  ENS_CUDA(c, cudaMemsetAsync(c->scratch, 0, sizeof(Scratch), s));
+  return ENS_OK;
+}
 
-ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int shorten) {
+// Enqueue one solve (no graph) with launch L.  frac < 1 runs the same systems
+// over a fraction of the horizon, for the tuner: phase mode keeps
+// max(1, round(frac n_phases)) phases (transient phases scaled alike),
+// event and plain mode integrate frac of [t0, t1], RK4 takes
+// max(1, round(frac n_steps)) steps.  A shortened solve reuses the claim
+// order the tuner computed (order_ready) instead of running its own pilot.
+ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, double frac = 1.0) {
+  const bool full = !(frac < 1.0);
   ENS_CUDA(c, cudaMemsetAsync(c->scratch, 0, sizeof(Scratch), s));
   if (c->solver == ENS_RK4) {
     Rk4Args a{};
@@ -246,9 +287,10 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int sh
     a.scratch = c->scratch;
     a.t0 = c->t0;
     a.dt = c->tol.dt0;
-    a.nsteps = shorten > 0 ? std::min<int64_t>(c->tol.n_steps, shorten) : c->tol.n_steps;
+    a.nsteps = full ? c->tol.n_steps
+                    : std::min<int64_t>(c->tol.n_steps, std::max<int64_t>(1, std::llround(frac * c->tol.n_steps)));
     ENS_CUDA(c, record_kernel_event(c, 0, s));
-    cudaError_t e = launch_rk4(c->sys, c->tol.prec == ENS_FP64_STRICT, a, L.block, s);
+    cudaError_t e = launch_rk4(c->sys, c->tol.prec == ENS_FP64_STRICT, a, L.block, spt_of(L), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "rk4 launch");
     ENS_CUDA(c, record_kernel_event(c, 1, s));
     c->kev_recorded = true;
@@ -258,31 +300,28 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, int sh
     set_err(c, "ENS_FP32X2 needs C10 = 21/5 (polytropic exponent 1.4) in every system");
     return ENS_ENOTSUP;
   }
+  if (spt_of(L) != 1) {
+    set_err(c, "the adaptive kernels run one system per thread (systems_per_thread 1)");
+    return ENS_ENOTSUP;
+  }
   AdaptArgs a = adapt_args(c);
-  if (shorten > 0) {
-    if (a.n_phases > 0) a.n_phases = std::min<int32_t>(a.n_phases, shorten);
-    else a.t1 = a.t0 + (a.t1 - a.t0) / 16.0;
+  if (!full) {
+    if (a.n_phases > 0) {
+      const int32_t np = (int32_t)std::max<long long>(1, std::llround(frac * a.n_phases));
+      const int32_t nt = std::min<int32_t>((int32_t)(frac * a.n_transient), np - 1);
+      a.n_phases = std::min(a.n_phases, np);
+      a.n_transient = std::max<int32_t>(0, std::min(a.n_transient, nt));
+      a.acc_phases = a.n_phases - a.n_transient;
+    } else {
+      a.t1 = a.t0 + (a.t1 - a.t0) * frac;
+    }
   }
   a.persistent = L.mode == ENS_LAUNCH_PERSISTENT;
-  if (a.persistent && L.cost_order && shorten == 0) {
-    // pilot: one phase (or 1/16 of the horizon) of every system in plain
-    // mode, then order systems by decreasing pilot step count.  The pilot
-    // only ranks the systems, so it runs at a tolerance of at least 1e-7: a
-    // quarter of the steps of a 1e-10 pilot, and on the 362 x 362
-    // Keller-Miksis sweep a whole solve 1.4 % faster with the same results
-    // (the claim order never changes what a system computes).
-    AdaptArgs p = a;
-    p.persistent = 0;
-    if (p.n_phases > 0) p.n_phases = 1;
-    else p.t1 = p.t0 + (p.t1 - p.t0) / 16.0;
-    p.rtol = p.rtol > kPilotTol ? p.rtol : kPilotTol;
-    p.atol = p.atol > kPilotTol ? p.atol : kPilotTol;
-    AdaptLaunch PL{(c->n + 127) / 128, 128};
-    cudaError_t e = launch_adaptive(c, p, PL, s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "pilot launch");
-    e = launch_order(c->nacc, c->n, c->order, c->hist, s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "order launch");
-    ENS_CUDA(c, cudaMemsetAsync(c->scratch, 0, sizeof(Scratch), s));
+  if (a.persistent && L.cost_order) {
+    if (full || !c->order_ready) {
+      ens_status st = enqueue_order(c, adapt_args(c), s);
+      if (st != ENS_OK) return st;
+    }
     a.order = c->order;
   }
   AdaptLaunch AL = adapt_launch(c, L);
@@ -383,7 +422,10 @@ ens_status check_tol(ens_ctx* c, ens_solver solver, ens_system sys, const ens_to
 
 namespace {
 
-std::map<std::tuple<int, int, int, int64_t, int, int>, ens_launch> g_tune_cache;
+// tuned launch and its candidate table per (system, solver, precision, n,
+// phases, transient phases, horizon, device)
+std::map<std::tuple<int, int, int, int64_t, int, int, double, int>, std::pair<ens_launch, std::vector<ens_tune_row>>>
+    g_tune_cache;
 
 }  // namespace
 
@@ -516,7 +558,11 @@ ens_status ens_set_launch(ens_ctx* c, const ens_launch* cfg) {
     return ENS_EINVAL;
   }
   if (c->solver == ENS_RK4 && L.mode != ENS_LAUNCH_PLAIN) {
-    set_err(c, "RK4 runs one system per thread (plain launch)");
+    set_err(c, "RK4 runs a plain launch (systems_per_thread systems per thread)");
+    return ENS_ENOTSUP;
+  }
+  if (c->solver != ENS_RK4 && spt_of(L) != 1) {
+    set_err(c, "the adaptive solvers run one system per thread (systems_per_thread 1)");
     return ENS_ENOTSUP;
   }
   c->launch = L;
@@ -535,7 +581,7 @@ ens_status ens_solve(ens_ctx* c, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
   if (c->n == 0) return ENS_OK;
-  if (!c->launch.use_graph) return enqueue_solve(c, c->launch, s, 0);
+  if (!c->launch.use_graph) return enqueue_solve(c, c->launch, s);
   if (!c->graph_valid || c->graph_stream != s) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
@@ -548,7 +594,7 @@ ens_status ens_solve(ens_ctx* c, void* stream) {
       cudaStreamDestroy(cap);
       return cuda_fail(c, e, "cudaStreamBeginCapture");
     }
-    ens_status st = enqueue_solve(c, c->launch, cap, 0);
+    ens_status st = enqueue_solve(c, c->launch, cap);
     e = cudaStreamEndCapture(cap, &g);
     cudaStreamDestroy(cap);
     if (st != ENS_OK) {
@@ -630,80 +676,146 @@ int32_t ens_npar(const ens_ctx* c) { return c ? c->npar : 0; }
 ens_status ens_autotune(ens_ctx* c, void* stream, ens_launch* best) {
   if (!c) return ENS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
   if (c->n == 0) {
     if (best) *best = c->launch;
     return ENS_OK;
   }
+  const double horizon = c->solver == ENS_RK4 ? (double)c->tol.n_steps : c->t1 - c->t0;
   const auto key = std::make_tuple((int)c->sys, (int)c->solver, (int)c->tol.prec, c->n,
-                                   (int)c->tol.n_phases, c->device);
+                                   (int)c->tol.n_phases, (int)c->tol.n_transient, horizon, c->device);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      c->launch = it->second;
+      const bool graph = c->launch.use_graph;
+      c->launch = it->second.first;
+      c->launch.use_graph = graph;
+      c->tune_rows = it->second.second;
       c->graph_valid = false;
       if (best) *best = c->launch;
       return ENS_OK;
     }
   }
-  std::vector<ens_launch> cands;
-  if (c->solver == ENS_RK4) {
-    for (int b : {32, 64, 128, 256}) {
-      ens_launch L{};
-      L.mode = ENS_LAUNCH_PLAIN;
-      L.block = b;
-      cands.push_back(L);
-    }
-  } else {
-    for (int b : {64, 128}) {
-      ens_launch L{};
-      L.mode = ENS_LAUNCH_PLAIN;
-      L.block = b;
-      cands.push_back(L);
-    }
-    const int shapes[][2] = {{32, 4}, {64, 2}, {128, 1}, {96, 1}, {160, 1}, {192, 1}, {128, 2}, {256, 1}};
-    for (const auto& sh : shapes) {
-      ens_launch L{};
-      L.mode = ENS_LAUNCH_PERSISTENT;
-      L.block = sh[0];
-      L.blocks_per_sm = sh[1];
-      cands.push_back(L);
-    }
-  }
-  const int shorten = c->solver == ENS_RK4 ? 200 : 2;
-  cudaEvent_t e0, e1;
-  ENS_CUDA(c, cudaEventCreate(&e0));
-  ENS_CUDA(c, cudaEventCreate(&e1));
-  float best_ms = 1e30f;
+  c->tune_rows.clear();
+  auto mk = [](int mode, int block, int bps, int co, int spt) {
+    ens_launch L{};
+    L.mode = mode;
+    L.block = block;
+    L.blocks_per_sm = bps;
+    L.cost_order = co;
+    L.systems_per_thread = spt;
+    return L;
+  };
+  // Time one candidate: the main kernel of a shortened solve (CUDA events
+  // recorded by enqueue_solve around that launch).
+  double frac = 1.0;
+  auto time_one = [&](const ens_launch& L, float* ms) -> ens_status {
+    ens_status st = enqueue_solve(c, L, s, frac);
+    if (st != ENS_OK) return st;
+    ENS_CUDA(c, cudaStreamSynchronize(s));
+    ENS_CUDA(c, cudaEventElapsedTime(ms, c->kev[0], c->kev[1]));
+    c->tune_rows.push_back(ens_tune_row{L, (double)*ms, frac});
+    return ENS_OK;
+  };
   ens_launch best_L = c->launch;
-  for (const ens_launch& L : cands) {
-    ens_status st = enqueue_solve(c, L, s, shorten);  // warm-up
-    if (st != ENS_OK) break;
-    ENS_CUDA(c, cudaEventRecord(e0, s));
-    st = enqueue_solve(c, L, s, shorten);
-    if (st != ENS_OK) break;
-    ENS_CUDA(c, cudaEventRecord(e1, s));
-    ENS_CUDA(c, cudaEventSynchronize(e1));
+  float best_ms = 1e30f;
+  auto consider = [&](const ens_launch& L) -> ens_status {
     float ms = 0.f;
-    ENS_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+    ens_status st = time_one(L, &ms);
+    if (st != ENS_OK) return st;
     if (ms < best_ms) {
       best_ms = ms;
       best_L = L;
     }
+    return ENS_OK;
+  };
+  ens_status st = ENS_OK;
+  if (c->solver == ENS_RK4) {
+    // fixed step: every system takes the same steps, so the shape only
+    // decides occupancy and ILP (systems per thread).  Whole solves up to
+    // 1e9 system-steps (Lorenz at N = 768,000 takes about 40 ms), else an
+    // eighth of the steps; each candidate runs twice (the first launch of a
+    // kernel variant includes its loading) and keeps the faster time.
+    frac = (double)c->n * (double)c->tol.n_steps <= 1e9 ? 1.0 : 0.125;
+    for (int spt : {1, 2, 4})
+      for (int b : {32, 64, 128, 256}) {
+        if (st != ENS_OK) break;
+        const ens_launch L = mk(ENS_LAUNCH_PLAIN, b, 0, 0, spt);
+        float ms0 = 0.f, ms1 = 0.f;
+        st = time_one(L, &ms0);
+        if (st == ENS_OK) st = time_one(L, &ms1);
+        if (st != ENS_OK) break;
+        c->tune_rows.erase(c->tune_rows.end() - 2);  // keep the second timing
+        if (std::min(ms0, ms1) < best_ms) {
+          best_ms = std::min(ms0, ms1);
+          best_L = L;
+        }
+      }
+  } else {
+    // Adaptive: the run time is the larger of the throughput bound (more
+    // warps per SM feed the FP64 pipe better) and the longest system's chain
+    // (every warp that shares an SM slows it).  Both scale with the horizon,
+    // so an eighth of the phases (or of the time span) of every system keeps
+    // the balance of the full solve.  The claim order comes from the same
+    // one-phase pilot as the full solve's and is computed once here.
+    frac = 0.125;
+    if (c->tol.n_phases > 0 && c->tol.n_phases < 8) frac = 1.0;
+    AdaptArgs a = adapt_args(c);
+    st = enqueue_order(c, a, s);
+    if (st == ENS_OK) c->order_ready = true;
+    // warm-up at the default shape; shrink the horizon while one shortened
+    // solve takes more than 0.6 s (down to one phase or 1/128 of the span)
+    float ms = 0.f;
+    const ens_launch L0 = mk(ENS_LAUNCH_PERSISTENT, 160, 1, 1, 1);
+    if (st == ENS_OK) st = enqueue_solve(c, L0, s, frac);
+    if (st == ENS_OK) {
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->kev[0], c->kev[1]);
+      if (e != cudaSuccess) st = cuda_fail(c, e, "autotune warm-up");
+    }
+    // at least two phases: the first one holds the transient from the initial state
+    const double min_frac = c->tol.n_phases > 0 ? 2.0 / c->tol.n_phases : 1.0 / 128;
+    while (st == ENS_OK && ms > 600.f) {
+      if (frac * 0.5 < min_frac) break;
+      frac *= 0.5;
+      ms *= 0.5f;
+    }
+    // warps per SM -> (block, blocks per SM)
+    const int shapes[][3] = {{3, 96, 1},  {4, 128, 1},  {5, 160, 1},  {6, 192, 1},  {7, 224, 1},
+                             {8, 256, 1}, {12, 192, 2}, {16, 256, 2}, {24, 256, 3}};
+    int best_w = 0;
+    for (const auto& sh : shapes) {
+      if (st != ENS_OK) break;
+      const float before = best_ms;
+      st = consider(mk(ENS_LAUNCH_PERSISTENT, sh[1], sh[2], 1, 1));
+      if (best_ms < before) best_w = sh[0];
+    }
+    // the same residency without longest-first claiming, and a plain launch
+    if (st == ENS_OK && best_w > 0) {
+      for (const auto& sh : shapes)
+        if (sh[0] == best_w) st = consider(mk(ENS_LAUNCH_PERSISTENT, sh[1], sh[2], 0, 1));
+    }
+    if (st == ENS_OK) st = consider(mk(ENS_LAUNCH_PLAIN, 128, 0, 0, 1));
+    c->order_ready = false;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (st != ENS_OK) return st;
   best_L.use_graph = c->launch.use_graph;
-  best_L.cost_order = c->launch.cost_order;
   c->launch = best_L;
   c->graph_valid = false;
-  c->last_stream = s;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = best_L;
+    g_tune_cache[key] = std::make_pair(best_L, c->tune_rows);
   }
   if (best) *best = best_L;
   return ENS_OK;
+}
+
+int32_t ens_autotune_table(const ens_ctx* c, ens_tune_row* rows, int32_t cap) {
+  if (!c) return 0;
+  const int32_t n = (int32_t)c->tune_rows.size();
+  for (int32_t k = 0; k < n && k < cap && rows; ++k) rows[k] = c->tune_rows[k];
+  return n;
 }
 
 ens_status ens_eval_rhs(ens_system sys, int64_t n, const double* params, const double* t, const double* y,

@@ -242,9 +242,15 @@ __global__ void km_labels_kernel(int64_t n, const double* acc, int n_phases, int
 // Deterministic stream compaction of {i : v[i] > thr} in increasing order.
 constexpr int kSelBlock = 1024;
 
-__global__ void select_count_kernel(int64_t n, const float* v, float thr, unsigned* counts) {
+// i is selected when v[i] > thr, or, with a second array w, when w[i] > thr_w
+__device__ __forceinline__ bool gate(int64_t i, int64_t n, const float* v, float thr, const float* w, float thr_w) {
+  return i < n && (v[i] > thr || (w != nullptr && w[i] > thr_w));
+}
+
+__global__ void select_count_kernel(int64_t n, const float* v, float thr, const float* w, float thr_w,
+                                    unsigned* counts) {
   const int64_t i = blockIdx.x * (int64_t)kSelBlock + threadIdx.x;
-  const int c = __syncthreads_count(i < n && v[i] > thr);
+  const int c = __syncthreads_count(gate(i, n, v, thr, w, thr_w));
   if (threadIdx.x == 0) counts[blockIdx.x] = (unsigned)c;
 }
 
@@ -276,10 +282,11 @@ __global__ void select_scan_kernel(unsigned* counts, int64_t nblocks, long long*
   }
 }
 
-__global__ void select_scatter_kernel(int64_t n, const float* v, float thr, const unsigned* offs, int32_t* idx) {
+__global__ void select_scatter_kernel(int64_t n, const float* v, float thr, const float* w, float thr_w,
+                                      const unsigned* offs, int32_t* idx) {
   __shared__ unsigned warp_base[kSelBlock / 32];
   const int64_t i = blockIdx.x * (int64_t)kSelBlock + threadIdx.x;
-  const bool flag = i < n && v[i] > thr;
+  const bool flag = gate(i, n, v, thr, w, thr_w);
   const unsigned ballot = __ballot_sync(0xffffffffu, flag);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) warp_base[warp] = __popc(ballot);
@@ -307,6 +314,50 @@ __global__ void gather_f64_kernel(int64_t k, const int32_t* idx, const double* s
 __global__ void scatter_f32_kernel(int64_t k, const int32_t* idx, const float* src, float* dst) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
     dst[idx[i]] = src[2 * i];
+}
+
+// Steepness of a map v on a rows x cols grid (row-major, columns fastest):
+// the largest |v(neighbour) - v| / distance over the up to four neighbours
+// `stride` points away (inv_dr, inv_dc: inverse distances at that stride).
+__global__ void grid_gradient_kernel(int64_t rows, int64_t cols, int64_t stride, const float* v, float inv_dr,
+                                     float inv_dc, float* g) {
+  const int64_t n = rows * cols;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / cols, c = i - r * cols;
+    const float v0 = v[i];
+    float m = 0.f;
+    if (r >= stride) m = fmaxf(m, fabsf(v[i - stride * cols] - v0) * inv_dr);
+    if (r + stride < rows) m = fmaxf(m, fabsf(v[i + stride * cols] - v0) * inv_dr);
+    if (c >= stride) m = fmaxf(m, fabsf(v[i - stride] - v0) * inv_dc);
+    if (c + stride < cols) m = fmaxf(m, fabsf(v[i + stride] - v0) * inv_dc);
+    g[i] = m;
+  }
+}
+
+// Five feature points per input point: x, x +- d0 along feature 0, x +- d1
+// along feature 1; out [5][n][2].
+__global__ void feature_stencil_kernel(int64_t n, const float* x, float d0, float d1, float* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float a = x[2 * i], b = x[2 * i + 1];
+    const float pa[5] = {a, a + d0, a - d0, a, a};
+    const float pb[5] = {b, b, b, b + d1, b - d1};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      out[2 * (k * n + i)] = pa[k];
+      out[2 * (k * n + i) + 1] = pb[k];
+    }
+  }
+}
+
+// Steepness at stencil centres from the map's values v [5][n] at the points
+// of feature_stencil_kernel: the grid gradient's definition on a stencil.
+__global__ void stencil_gradient_kernel(int64_t n, const float* v, float inv_d0, float inv_d1, float* g) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v0 = v[i];
+    float m = fmaxf(fabsf(v[n + i] - v0), fabsf(v[2 * n + i] - v0)) * inv_d0;
+    m = fmaxf(m, fmaxf(fabsf(v[3 * n + i] - v0), fabsf(v[4 * n + i] - v0)) * inv_d1);
+    g[i] = m;
+  }
 }
 
 }  // namespace
@@ -624,13 +675,14 @@ ens_status ens_km_labels(int64_t n, const double* acc, int32_t n_phases, int32_t
   return cudaGetLastError() == cudaSuccess ? ENS_OK : ENS_ECUDA;
 }
 
-ens_status ens_select_above(int64_t n, const float* v, float thr, int32_t* idx, int64_t* count, void* stream) {
+ens_status ens_select_gate(int64_t n, const float* v, float thr, const float* w, float thr_w, int32_t* idx,
+                           int64_t* count, void* stream) {
   if (n < 0 || !count) return ENS_EINVAL;
   if (n == 0) {
     *count = 0;
     return ENS_OK;
   }
-  if (n > 0x7fffffffLL || !is_device(v) || !is_device(idx)) return ENS_EINVAL;
+  if (n > 0x7fffffffLL || !is_device(v) || !is_device(idx) || (w && !is_device(w))) return ENS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t nb = (n + kSelBlock - 1) / kSelBlock;
   unsigned* counts = nullptr;
@@ -640,9 +692,9 @@ ens_status ens_select_above(int64_t n, const float* v, float thr, int32_t* idx, 
     cudaFree(counts);
     return ENS_ENOMEM;
   }
-  select_count_kernel<<<(unsigned)nb, kSelBlock, 0, s>>>(n, v, thr, counts);
+  select_count_kernel<<<(unsigned)nb, kSelBlock, 0, s>>>(n, v, thr, w, thr_w, counts);
   select_scan_kernel<<<1, 1024, 0, s>>>(counts, nb, total);
-  select_scatter_kernel<<<(unsigned)nb, kSelBlock, 0, s>>>(n, v, thr, counts, idx);
+  select_scatter_kernel<<<(unsigned)nb, kSelBlock, 0, s>>>(n, v, thr, w, thr_w, counts, idx);
   long long t = 0;
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&t, total, sizeof(long long), cudaMemcpyDeviceToHost, s);
@@ -652,6 +704,36 @@ ens_status ens_select_above(int64_t n, const float* v, float thr, int32_t* idx, 
   if (e != cudaSuccess) return ENS_ECUDA;
   *count = t;
   return ENS_OK;
+}
+
+ens_status ens_select_above(int64_t n, const float* v, float thr, int32_t* idx, int64_t* count, void* stream) {
+  return ens_select_gate(n, v, thr, nullptr, 0.f, idx, count, stream);
+}
+
+ens_status ens_grid_gradient(int64_t rows, int64_t cols, int64_t stride, const float* v, float d_row, float d_col,
+                             float* g, void* stream) {
+  if (rows < 0 || cols < 0 || stride < 1 || !(d_row > 0.f) || !(d_col > 0.f)) return ENS_EINVAL;
+  if (rows == 0 || cols == 0) return ENS_OK;
+  if (!is_device(v) || !is_device(g)) return ENS_EINVAL;
+  grid_gradient_kernel<<<grid_for(rows * cols), 256, 0, (cudaStream_t)stream>>>(
+      rows, cols, stride, v, 1.f / (d_row * stride), 1.f / (d_col * stride), g);
+  return cudaGetLastError() == cudaSuccess ? ENS_OK : ENS_ECUDA;
+}
+
+ens_status ens_feature_stencil(int64_t n, const float* x, float d0, float d1, float* out, void* stream) {
+  if (n < 0 || !(d0 > 0.f) || !(d1 > 0.f)) return ENS_EINVAL;
+  if (n == 0) return ENS_OK;
+  if (!is_device(x) || !is_device(out)) return ENS_EINVAL;
+  feature_stencil_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, x, d0, d1, out);
+  return cudaGetLastError() == cudaSuccess ? ENS_OK : ENS_ECUDA;
+}
+
+ens_status ens_stencil_gradient(int64_t n, const float* v, float d0, float d1, float* g, void* stream) {
+  if (n < 0 || !(d0 > 0.f) || !(d1 > 0.f)) return ENS_EINVAL;
+  if (n == 0) return ENS_OK;
+  if (!is_device(v) || !is_device(g)) return ENS_EINVAL;
+  stencil_gradient_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, v, 1.f / d0, 1.f / d1, g);
+  return cudaGetLastError() == cudaSuccess ? ENS_OK : ENS_ECUDA;
 }
 
 ens_status ens_gather_f64(int64_t k, const int32_t* idx, const double* src, double* dst, void* stream) {

@@ -166,6 +166,27 @@ def screen_grid(m: int = 4096, pa_min: float = 2.0e5 / 361, pa_max: float = 2.0e
     return PA.ravel().copy(), F.ravel().copy()
 
 
+def screen_subgrid(m: int, stride: int) -> np.ndarray:
+    """Flat indices of the points of the m x m screening grid on every
+    stride-th row and column (a uniform 1/stride^2 sample of the grid)."""
+    r = np.arange(0, m, stride)
+    return (r[:, None] * m + r[None, :]).ravel()
+
+
+def screen_calibration_points(m: int, k: int, stride: int, seed: int = SEED + 3) -> np.ndarray:
+    """k distinct random flat indices of the m x m screening grid that avoid
+    the stride sub-grid of screen_subgrid (so a calibration sample drawn here
+    never overlaps the validation sample drawn there); sorted."""
+    rng = np.random.default_rng(seed)
+    out = np.empty(0, dtype=np.int64)
+    while out.size < k:
+        cand = rng.integers(0, m * m, 2 * k)
+        r, c = cand // m, cand % m
+        cand = cand[(r % stride != 0) | (c % stride != 0)]
+        out = np.unique(np.concatenate([out, cand]))
+    return np.sort(rng.choice(out, k, replace=False))
+
+
 def subsample(n: int, k: int, seed: int = SEED, strata: int = 64) -> np.ndarray:
     """Sorted stratified sample of k indices out of range(n): the index range
     is cut into `strata` equal blocks and k / strata indices are drawn from

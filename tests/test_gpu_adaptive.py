@@ -327,17 +327,54 @@ def test_kernel_ms_times_the_main_launch(use_graph):
         ens.ens_destroy(ctx)
 
 
-def test_autotune_returns_a_valid_launch():
-    km = W.km(16, 16, n_phases=2)
+def test_autotune_of_the_adaptive_solve():
+    """The tuner times persistent launches of 3-24 warps per SM with
+    longest-first claiming, the best residency without it and a plain launch,
+    on a shortened horizon of every system (1/8 of 16 phases), keeps the
+    fastest, and leaves results unchanged: the claim order and the launch
+    shape never change what a system computes."""
+    km = W.km(24, 20, n_phases=16)
     C = km_coeffs_lib(km["phys"], km["liquid"])
     ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
                          ens.ENS_RKCK45, ens_tol_from(km["tol"]))
     try:
-        best = ens.ens_autotune(ctx)
-        assert best.mode in (ens.ENS_LAUNCH_PLAIN, ens.ENS_LAUNCH_PERSISTENT)
-        assert best.block % 32 == 0
         ens.ens_solve(ctx)
         assert ens.ens_sync(ctx) == ens.ENS_OK
+        ref = {w: ens.ens_read(ctx, w) for w in (ens.ENS_ACC, ens.ENS_STATE, ens.ENS_NSTEPS)}
+        best = ens.ens_autotune(ctx)
+        rows = ens.ens_autotune_table(ctx)
+        assert len(rows) == 11
+        assert all(r["horizon_frac"] == 0.125 for r in rows)
+        persistent = [r for r in rows if r["launch"]["mode"] == ens.ENS_LAUNCH_PERSISTENT]
+        warps = {r["launch"]["block"] // 32 * r["launch"]["blocks_per_sm"] for r in persistent}
+        assert warps == {3, 4, 5, 6, 7, 8, 12, 16, 24}
+        assert any(r["launch"]["mode"] == ens.ENS_LAUNCH_PLAIN for r in rows)
+        assert any(r["launch"]["cost_order"] == 0 for r in persistent)
+        fastest = min(rows, key=lambda r: r["ms"])["launch"]
+        assert (fastest["mode"], fastest["block"], fastest["blocks_per_sm"], fastest["cost_order"]) == \
+            (best.mode, best.block, best.blocks_per_sm, best.cost_order)
+        ens.ens_solve(ctx)
+        assert ens.ens_sync(ctx) == ens.ENS_OK
+        for w, v in ref.items():
+            assert np.array_equal(ens.ens_read(ctx, w), v)
+        # a second call returns the cached choice and table
+        again = ens.ens_autotune(ctx)
+        assert (again.block, again.blocks_per_sm) == (best.block, best.blocks_per_sm)
+        assert len(ens.ens_autotune_table(ctx)) == len(rows)
+    finally:
+        ens.ens_destroy(ctx)
+
+
+def test_adaptive_solvers_refuse_several_systems_per_thread():
+    km = W.km(4, 4, n_phases=2)
+    C = km_coeffs_lib(km["phys"], km["liquid"])
+    ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
+                         ens.ENS_RKCK45, ens_tol_from(km["tol"]))
+    try:
+        with pytest.raises(ens.EnsError) as e:
+            ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1, systems_per_thread=2))
+        assert e.value.status == ens.ENS_ENOTSUP
+        assert ens.ens_get_launch(ctx).systems_per_thread in (0, 1)
     finally:
         ens.ens_destroy(ctx)
 

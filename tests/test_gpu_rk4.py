@@ -119,3 +119,48 @@ def test_device_inputs_and_destinations():
         ens.ens_destroy(ctx)
     yo, _ = oracle.rk4_solve(oracle.LORENZ, wl["params"], wl["y0"], 0.0, wl["dt"], 100)
     assert rel_err(dst.cpu().numpy(), yo).max() < 1e-12
+
+
+@pytest.mark.parametrize("prec", [ens.ENS_FP64, ens.ENS_FP64_STRICT])
+@pytest.mark.parametrize("spt,block", [(2, 64), (4, 32), (4, 128)])
+def test_systems_per_thread_gives_the_same_bits(prec, spt, block):
+    """Two or four systems interleaved per thread run each system's steps
+    with the arithmetic of one system per thread: every output is bitwise the
+    same, including the ragged end of the ensemble (1,001 systems do not fill
+    the last block's slots), and the strict flavour still equals the oracle."""
+    wl = W.lorenz(1001)
+    ref = _rk4(ens.ENS_SYS_LORENZ, wl, prec=prec, nsteps=300,
+               launch=ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=32))
+    got = _rk4(ens.ENS_SYS_LORENZ, wl, prec=prec, nsteps=300,
+               launch=ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=block, systems_per_thread=spt))
+    assert got["sync"] == ens.ENS_OK
+    for k in ("y", "status", "nacc", "nrhs"):
+        assert np.array_equal(got[k], ref[k]), k
+    if prec == ens.ENS_FP64_STRICT:
+        yo, _ = oracle.rk4_solve(oracle.LORENZ, wl["params"], wl["y0"], 0.0, wl["dt"], 300)
+        assert np.array_equal(got["y"], yo)
+
+
+def test_autotune_of_rk4_searches_systems_per_thread():
+    """The tuner times block sizes x systems per thread on whole solves, keeps
+    the fastest, and the tuned solve gives the untuned solve's bits."""
+    wl = W.lorenz(4096)
+    tol = ens.make_tol(dt0=wl["dt"], n_steps=200)
+    ctx = ens.ens_create(ens.ENS_SYS_LORENZ, 4096, wl["params"], wl["y0"], (0.0, 0.0), ens.ENS_RK4, tol)
+    try:
+        ens.ens_solve(ctx)
+        ens.ens_sync(ctx)
+        ref = ens.ens_read(ctx, ens.ENS_STATE)
+        best = ens.ens_autotune(ctx)
+        rows = ens.ens_autotune_table(ctx)
+        assert len(rows) == 12
+        assert {r["launch"]["systems_per_thread"] for r in rows} == {1, 2, 4}
+        fastest = min(rows, key=lambda r: r["ms"])
+        assert fastest["launch"]["block"] == best.block
+        assert fastest["launch"]["systems_per_thread"] == max(1, best.systems_per_thread)
+        assert ens.ens_get_launch(ctx).block == best.block
+        ens.ens_solve(ctx)
+        assert ens.ens_sync(ctx) == ens.ENS_OK
+        assert np.array_equal(ens.ens_read(ctx, ens.ENS_STATE), ref)
+    finally:
+        ens.ens_destroy(ctx)
