@@ -41,7 +41,7 @@ FP64_INST_PER_KM_TRIAL = 367.29
 # DRAM bytes (read + write) of one benchmarked Keller-Miksis launch, from the
 # one-pass ncu capture in profiles/ (inputs 15.7 MB read once, 134 MB of
 # per-period accessories written once); None once the kernel changes.
-KM_LAUNCH_DRAM_BYTES = None
+KM_LAUNCH_DRAM_BYTES = 37893888 + 120424704
 FLOPS_PER_X2P_STEP = 21.0     # 10 DFMA + 1 DADD (Sec. 3.2.2 counters; kernel counted by ncu)
 FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast kernel
 # executed flops per trial of the other adaptive kernels (ncu counts,
@@ -408,7 +408,8 @@ def configs_summary(value, roofline, sec, n_headline):
             "err_unflagged": _r({k: val["err_unflagged"][k] for k in ("p90", "p99", "max")}, 3),
             "fallback": _r(sc["fallback_fraction"], 3), "p1_err": _r(val["period1_error_rate_unflagged"], 3),
             "x": _r(sc["speedup"], 3), "x_incl_fixed": _r(sc["speedup_incl_fixed"], 3),
-            "fp64_1024sq_s": _r(val["fp64_s"], 3)}
+            "fp64_1024sq_s": _r(val["fp64_s"], 3),
+            "x_est_by_bound": {str(c["bound"]): _r(c["speedup_est"], 3) for c in sc.get("bound_curve", [])}}
     return out
 
 
@@ -852,12 +853,48 @@ def run_secondary(ens, torch, stream, dev, tuned=True):
     kms = ens.ens_kernel_ms(ctx)
     nacc = ens.ens_read(ctx, ens.ENS_NSTEPS)
     nrej = ens.ens_read(ctx, ens.ENS_NREJ)
+    acc64 = torch.empty((35, 262144), dtype=torch.float64, device=dev)
+    ens.ens_read(ctx, ens.ENS_ACC, acc64)
     ens.ens_destroy(ctx)
     trials = float(nacc.sum() + nrej.sum())
     out["relief_valve_262144"] = {"ms": ms, "kernel_ms": kms, "status": st, "value": float(nacc.sum()) / (ms / 1e3),
                                   "unit": "system-steps/s", "trials": trials, "launch": L.as_dict(), "tune_s": tune_s,
                                   "fp64_frac": (FLOPS_PER_VALVE_TRIAL * trials / (kms / 1e3) / FP64_PEAK
                                                 if FLOPS_PER_VALVE_TRIAL else None)}
+    # the same sweep in double-float arithmetic (state, stages, right-hand
+    # side and controller as float pairs; time, events, impact law and
+    # sticking in FP64): speedup, event counts and value rows against FP64
+    tol2 = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
+                        event_tol=t.event_tol, acc_t_start=t.acc_t_start, timeout_s=900.0, prec=ens.ENS_FP32X2)
+    ctx = ens.ens_create(ens.ENS_SYS_RELIEF_VALVE, 262144, wl["params"], wl["y0"], (t.t0, t.t1),
+                         ens.ENS_RKCK45, tol2)
+    ens.ens_set_launch(ctx, ens.make_launch(block=256, blocks_per_sm=1, use_graph=1, cost_order=1))
+    tune2 = None
+    if tuned:
+        t0 = time.perf_counter()
+        ens.ens_autotune(ctx, stream)
+        tune2 = time.perf_counter() - t0
+    L2 = ens.ens_get_launch(ctx)
+    e0.record(stream)
+    ens.ens_solve(ctx, stream)
+    e1.record(stream)
+    st2 = ens.ens_sync(ctx)
+    ms2 = e0.elapsed_time(e1)
+    kms2 = ens.ens_kernel_ms(ctx)
+    nacc2 = ens.ens_read(ctx, ens.ENS_NSTEPS)
+    acc2 = torch.empty((35, 262144), dtype=torch.float64, device=dev)
+    ens.ens_read(ctx, ens.ENS_ACC, acc2)
+    ens.ens_destroy(ctx)
+    same_events = (acc2[33:35] == acc64[33:35]).all(dim=0)
+    d = (acc2[:33] - acc64[:33]).abs()
+    d = torch.where(torch.isnan(acc2[:33]) & torch.isnan(acc64[:33]), torch.zeros_like(d), d)
+    rel = (d.amax(dim=0) / acc64[:33].abs().nan_to_num(0.0).amax(dim=0).clamp_min(1e-300))[same_events]
+    q = _quantiles(rel, torch)
+    out["relief_valve_262144"]["fp32x2"] = {
+        "ms": ms2, "kernel_ms": kms2, "s": ms2 / 1e3, "status": st2, "value": float(nacc2.sum()) / (ms2 / 1e3),
+        "speedup": ms / ms2, "launch": L2.as_dict(), "tune_s": tune2,
+        "same_event_counts": float(same_events.double().mean()),
+        "value_rows_rel_diff_vs_fp64": q, "err_p99": q["p99"]}
     return out
 
 
@@ -1035,11 +1072,12 @@ def run_profile_case(case: str):
                           "flop_per_launch_per_kernel": 3 * 2 * 128 * 128 * 1024 * 4,
                           "loss": [float(hist[0].mean()), float(hist[-1].mean())]}), flush=True)
         return
-    elif case == "prv":
+    elif case in ("prv", "prv_df"):
         wl = W.prv(8192, t1=64.0)
         t = wl["tol"]
         tol = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
-                           event_tol=t.event_tol, acc_t_start=t.acc_t_start)
+                           event_tol=t.event_tol, acc_t_start=t.acc_t_start,
+                           prec=ens.ENS_FP32X2 if case == "prv_df" else ens.ENS_FP64)
         ctx = ens.ens_create(ens.ENS_SYS_RELIEF_VALVE, 8192, wl["params"], wl["y0"], (t.t0, t.t1),
                              ens.ENS_RKCK45, tol)
     elif case in ("x2p", "lorenz"):
@@ -1065,7 +1103,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile", default=None,
                     help="run one small case for ncu (km, km_full64, km_full2, km_fp32c, km_fp32x2, mlp_screen, "
-                         "mlp_screen_mma, mlp_train, prv, x2p, lorenz)")
+                         "mlp_screen_mma, mlp_train, prv, prv_df, x2p, lorenz)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)

@@ -18,6 +18,7 @@ cudaError_t launch_rk4(int sys, bool strict, const Rk4Args& a, int block, int sp
 cudaError_t launch_ck45(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_ck45_fp32c(unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_ck45_df(unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
+cudaError_t launch_ck45_df_events(const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_order(const int64_t* steps, int64_t n, int32_t* order, unsigned* hist,
                          cudaStream_t s);
 cudaError_t launch_rhs_eval(int sys, unsigned flags, int64_t n, const double* P, const double* t,
@@ -181,7 +182,8 @@ uint64_t timeout_ns(const ens_tol& t) {
 // the adaptive kernel of the context's precision
 cudaError_t launch_adaptive(const ens_ctx* c, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s) {
   if (c->tol.prec == ENS_FP32_COMP) return launch_ck45_fp32c(c->km_flags, a, L, s);
-  if (c->tol.prec == ENS_FP32X2) return launch_ck45_df(c->km_flags, a, L, s);
+  if (c->tol.prec == ENS_FP32X2)
+    return c->sys == ENS_SYS_RELIEF_VALVE ? launch_ck45_df_events(a, L, s) : launch_ck45_df(c->km_flags, a, L, s);
   return launch_ck45(c->sys, c->km_flags, a, L, s);
 }
 
@@ -406,9 +408,14 @@ ens_status check_tol(ens_ctx* c, ens_solver solver, ens_system sys, const ens_to
     set_err(c, "the relief valve runs in event mode (n_phases must be 0)");
     return ENS_ENOTSUP;
   }
-  if ((t.prec == ENS_FP32_COMP || t.prec == ENS_FP32X2) &&
-      !(sys == ENS_SYS_KELLER_MIKSIS && t.n_phases > 0 && solver == ENS_RKCK45)) {
-    set_err(c, "ENS_FP32_COMP and ENS_FP32X2 are implemented for the Keller-Miksis phase mode with Cash-Karp");
+  if (t.prec == ENS_FP32_COMP && !(sys == ENS_SYS_KELLER_MIKSIS && t.n_phases > 0 && solver == ENS_RKCK45)) {
+    set_err(c, "ENS_FP32_COMP is implemented for the Keller-Miksis phase mode with Cash-Karp");
+    return ENS_ENOTSUP;
+  }
+  if (t.prec == ENS_FP32X2 && !(solver == ENS_RKCK45 && ((sys == ENS_SYS_KELLER_MIKSIS && t.n_phases > 0) ||
+                                                          (sys == ENS_SYS_RELIEF_VALVE && t.n_phases == 0)))) {
+    set_err(c, "ENS_FP32X2 is implemented with Cash-Karp for the Keller-Miksis phase mode and the relief "
+               "valve's event mode");
     return ENS_ENOTSUP;
   }
   if (t.prec != ENS_FP64 && t.prec != ENS_FP32_COMP && t.prec != ENS_FP32X2) {

@@ -133,6 +133,27 @@ __host__ __device__ __forceinline__ DF inv_fifth_root(DF x) {
   return add(make(v), mul(mul(r, c), v));
 }
 
+// sqrt(x) for x >= 0 (0 for x <= 0 or NaN): the correctly rounded float
+// square root s0 of x.hi, then one Newton step s0 + r / (2 s0) on the
+// residual r = x - s0^2.  s0^2 = p.hi + p.lo exactly (two_prod) and x.hi -
+// p.hi is exact (the two are within a factor 2, Sterbenz), so r carries a
+// float's relative accuracy; Newton's quadratic convergence leaves about
+// u^2 s of the error of s0 (which includes x.lo), plus the float rounding
+// of the correction: within 4 u^2 relative (tests/test_df_host.py).
+__host__ __device__ __forceinline__ DF sqrt(DF x) {
+  if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
+#ifdef __CUDA_ARCH__
+  const float s0 = __fsqrt_rn(x.hi);
+  const float inv2 = 0.5f * __frcp_rn(s0);
+#else
+  const float s0 = std::sqrt(x.hi);
+  const float inv2 = 0.5f / s0;
+#endif
+  const DF p = two_prod(s0, s0);
+  const float r = ((x.hi - p.hi) - p.lo) + x.lo;
+  return fast_two_sum(s0, r * inv2);
+}
+
 // double <-> double-word through the integer pipe (a conversion instruction
 // costs about one FP64 pipe slot on this part).  trunc_f truncates the
 // significand of a double to 24 bits with the exponent rebiased; |x| below

@@ -17,8 +17,11 @@
 // instead of 1e-16, so results agree with the FP64 kernel to the sensitivity
 // of each system to such perturbations.
 #include "common.cuh"
+#include "events.cuh"
+#include "fcmp.cuh"
 #include "km_df.cuh"
 #include "rhs.cuh"
+#include "valve_df.cuh"
 
 namespace ens {
 
@@ -271,6 +274,244 @@ __global__ void __launch_bounds__(256) ck_phased_df_kernel(AdaptArgs a) {
       if (i >= 0) start_system(i);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Relief valve (event mode, Sec. 4.3) in double-float arithmetic.  The state,
+// the stage states and slopes, the right-hand side (valve_df.cuh, with a
+// double-word square root), the fifth-order update, the error estimate and
+// the controller are pairs on the FP32 pipes.  FP64 keeps the time t, the
+// step h, the event tests and root estimates (event_frac), the impact law
+// y2 <- -r y2 and the closed-form sticking interval: the steps whose result
+// decides where an event lies.  The valve's right-hand side does not depend
+// on t, so a trial needs no FP64 work besides the conversions of the state
+// that the event tests read.  Every rule is that of ck_events_kernel
+// (rkck45.cu): overshoot beyond the band |g| <= event_tol discards the trial
+// and retries with the step cut to the earliest estimated root (one half when
+// the impact starts inside the band, at most 40 retries); otherwise the step
+// is accepted and events are located at its end; a rebound whose apex stays
+// inside the band leaves the valve on the seat until y3 = delta.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) ck_events_df_kernel(AdaptArgs a) {
+  using namespace df;
+  constexpr int D = 3;
+  const uint64_t deadline = global_ns() + a.timeout_ns;
+  const double etol = a.event_tol;
+  const long long kt = okey(etol), knt = okey(-etol);
+  int64_t i = -1;
+  if (a.persistent) {
+    const unsigned long long k = atomicAdd(&a.scratch->next, 1ULL);
+    if (k < (unsigned long long)a.n) i = a.order ? (int64_t)a.order[k] : (int64_t)k;
+  } else {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g < a.n) i = g;
+  }
+  bool timed_out = false;
+  ValveDF s;
+  const DF rtol = from_double(a.rtol), atol = from_double(a.atol);
+  DF y[D], k1[D];
+  double t = a.t0, dt = a.dt0, h_ev = 0.0, ymin = 0.0;
+  int32_t st = 0, ev_retries = 0;
+  uint32_t trials = 0, nacc = 0, nrej = 0, nrhs = 0, nmax = 0, nimp = 0, iter = 0;
+  bool k1v = false, stuck = false;
+
+  auto start_system = [&](int64_t sys) {
+    s.load(a.params, a.n, sys);
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = from_double(a.y0[c * a.n + sys]);
+    t = a.t0;
+    dt = a.dt0;
+    h_ev = 0.0;
+    st = timed_out ? kStTimeout : 0;
+    ev_retries = 0;
+    trials = nacc = nrej = nrhs = nmax = nimp = 0;
+    k1v = false;
+    stuck = false;
+    ymin = (t >= a.acc_t_start) ? a.y0[sys] : __longlong_as_double(0x7ff0000000000000LL);
+    for (int r = 0; r < kRing; ++r)
+      a.acc[(int64_t)r * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
+  };
+  auto finish_system = [&](int64_t sys) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) a.y[c * a.n + sys] = to_double(y[c]);
+    a.acc[(int64_t)kRing * a.n + sys] = ymin;
+    a.acc[(int64_t)(kRing + 1) * a.n + sys] = (double)nmax;
+    a.acc[(int64_t)(kRing + 2) * a.n + sys] = (double)nimp;
+    a.t_out[sys] = t;
+    a.dt_out[sys] = dt;
+    a.status[sys] = st;
+    a.nacc[sys] = nacc;
+    a.nrej[sys] = nrej;
+    a.nrhs[sys] = nrhs;
+    if (st) atomicOr(&a.scratch->any_status, (unsigned)st);
+  };
+  auto claim_next = [&]() -> int64_t {
+    if (!a.persistent) return -1;
+    const unsigned long long k = atomicAdd(&a.scratch->next, 1ULL);
+    if (k >= (unsigned long long)a.n) return -1;
+    return a.order ? (int64_t)a.order[k] : (int64_t)k;
+  };
+
+  if (i >= 0) start_system(i);
+  while (i >= 0) {
+    bool sys_done = false;
+    if (st == 0) {
+      if ((++iter & 127u) == 0 && global_ns() > deadline) timed_out = true;
+      if (timed_out) st |= kStTimeout;
+      else if (!stuck && trials >= (uint64_t)a.max_steps) st |= kStMaxSteps;
+    }
+    if (st != 0) {
+      sys_done = true;
+    } else if (stuck) {
+      // closed-form interval on the seat: y1 = y2 = 0, y3' = beta q
+      const double y3 = to_double(y[2]);
+      const double t_lift = t + (s.deltad - y3) / (s.betad * s.qd);
+      if (t_lift >= a.t1) {
+        y[2] = from_double(y3 + s.betad * s.qd * (a.t1 - t));
+        t = a.t1;
+      } else {
+        y[2] = s.delta;
+        t = t_lift;
+        stuck = false;
+      }
+      k1v = false;
+      if (okey(t) >= okey(a.acc_t_start) && okey(0.0) < okey(ymin)) ymin = 0.0;
+      if (okey(t) >= okey(a.t1)) sys_done = true;
+    } else {
+      double h = dt;
+      int limited = 0;
+      const double rest = a.t1 - t;  // > 0 before the end
+      if (nnbits(h) >= nnbits(rest)) {
+        h = rest;
+        limited = 1;
+      }
+      if (nnbits(h_ev) > 0 && nnbits(h_ev) < nnbits(h)) {  // h_ev >= 0
+        h = h_ev;
+        limited = 2;
+      }
+      if (!k1v) {
+        s.f(y, k1);
+        ++nrhs;
+        k1v = true;
+      }
+      const DF hd = from_double(h);
+      DF k2[D], k3[D], k4[D], k5[D], k6[D], x[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) x[c] = add(y[c], mul(mul(A21, k1[c]), hd));
+      s.f(x, k2);
+#pragma unroll
+      for (int c = 0; c < D; ++c) x[c] = add(y[c], mul(df::fma(A32, k2[c], mul(A31, k1[c])), hd));
+      s.f(x, k3);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        x[c] = add(y[c], mul(df::fma(A43, k3[c], df::fma(A42, k2[c], mul(A41, k1[c]))), hd));
+      s.f(x, k4);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        x[c] = add(y[c],
+                   mul(df::fma(A54, k4[c], df::fma(A53, k3[c], df::fma(A52, k2[c], mul(A51, k1[c])))), hd));
+      s.f(x, k5);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        x[c] = add(y[c], mul(df::fma(A65, k5[c],
+                                     df::fma(A64, k4[c], df::fma(A63, k3[c], df::fma(A62, k2[c], mul(A61, k1[c]))))),
+                             hd));
+      s.f(x, k6);
+      nrhs += 5;
+      ++trials;
+      // fifth-order solution, error estimate and error norm
+      DF n[D], E = make(0.0f);
+      bool nan = false;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        n[c] = add(y[c], mul(df::fma(B6, k6[c], df::fma(B4, k4[c], df::fma(B3, k3[c], mul(B1, k1[c])))), hd));
+        const DF e = mul(df::fma(D6, k6[c], df::fma(D5, k5[c], df::fma(D4, k4[c], df::fma(D3, k3[c], mul(D1, k1[c]))))),
+                         hd);
+        const DF sc = df::fma(rtol, dmax(dabs(y[c]), dabs(n[c])), atol);
+        const DF r = mul(dabs(e), rcp(sc));
+        nan |= isnan(r.hi) || isnan(n[c].hi);
+        E = dmax(E, r);
+      }
+      DF fac;
+      if (nan) {
+        fac = make(0.2f);
+      } else {
+        const DF Ec = E.hi < 1e-4f ? pair_of(1e-4) : (E.hi > 2000.0f ? make(2000.0f) : E);
+        fac = mul(kSafety, inv_fifth_root(Ec));
+        fac = fac.hi < 0.2f ? make(0.2f) : fac;
+        fac = fac.hi > 5.0f ? make(5.0f) : fac;
+      }
+      const double facd = to_double(fac);
+      if (nan || gt(E, make(1.0f))) {
+        ++nrej;
+        dt = h * facd;
+        h_ev = 0.0;
+        if (nnbits(dt) < nnbits(a.dt_min)) st |= kStDtUnderflow;
+      } else {
+        // events: decided in FP64 on the state at both ends of the trial
+        const double y0d = to_double(y[0]), y1d = to_double(y[1]);
+        const double n0d = to_double(n[0]), n1d = to_double(n[1]);
+        double best = 2.0;
+        bool overshoot = false;
+        if (okey(n0d) < knt) {  // impact beyond the band
+          const double frac = (okey(y0d) > kt) ? event_frac(y0d, to_double(k1[0]), n0d, h) : 0.5;
+          best = nnmin(frac, best);
+          overshoot = true;
+        }
+        if (okey(y1d) > kt && okey(n1d) < knt) {  // maximum beyond the band
+          const double frac = event_frac(y1d, to_double(k1[1]), n1d, h);
+          best = nnmin(frac, best);
+          overshoot = true;
+        }
+        if (overshoot) {
+          if (++ev_retries > kEventRetries) st |= kStEventNoConverge;
+          else h_ev = h * best;
+        } else {
+#pragma unroll
+          for (int c = 0; c < D; ++c) y[c] = n[c];
+          t = (limited == 1) ? a.t1 : t + h;
+          k1v = false;
+          ++nacc;
+          ev_retries = 0;
+          h_ev = 0.0;
+          if (!limited) dt = bounded_step(h, facd, a.dt_min, a.dt_max);
+          double cur0 = n0d;
+          if (okey(y1d) > kt && nnbits(absd(n1d)) <= nnbits(etol)) {  // Poincare point
+            a.acc[(int64_t)(nmax % kRing) * a.n + i] = n0d;
+            ++nmax;
+          }
+          // impact law (Eqs. impact_law_1-3) in FP64: y1 <- 0, y2 <- -r y2
+          if (nnbits(absd(n0d)) <= nnbits(etol) && okey(n1d) < -1LL) {
+            const double v = -s.r * n1d;
+            y[0] = make(0.0f);
+            y[1] = from_double(v);
+            cur0 = 0.0;
+            ++nimp;
+            const double push = s.deltad - to_double(y[2]);
+            if (push > 0.0 && v * v <= 2.0 * push * etol) {
+              y[1] = make(0.0f);
+              stuck = true;
+            }
+          }
+          if (okey(t) >= okey(a.acc_t_start) && okey(cur0) < okey(ymin)) ymin = cur0;
+          if (okey(t) >= okey(a.t1)) sys_done = true;
+        }
+      }
+    }
+    if (sys_done) {
+      finish_system(i);
+      i = claim_next();
+      if (i >= 0) start_system(i);
+    }
+  }
+}
+
+cudaError_t launch_ck45_df_events(const AdaptArgs& a, AdaptLaunch L, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  if (a.n_phases != 0 || a.pair != kCashKarp) return cudaErrorInvalidValue;
+  if (L.grid <= 0 || L.grid > 0x7fffffffLL || L.block <= 0) return cudaErrorInvalidConfiguration;
+  ck_events_df_kernel<<<dim3((unsigned)L.grid), dim3((unsigned)L.block), 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ck45_df(unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s) {

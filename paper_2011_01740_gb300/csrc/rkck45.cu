@@ -26,6 +26,8 @@
 // and a wall-clock budget read from %globaltimer; there are no spin-waits.
 #include "common.cuh"
 #include "dual.cuh"
+#include "events.cuh"
+#include "fcmp.cuh"
 #include "rhs.cuh"
 
 namespace ens {
@@ -144,30 +146,6 @@ __device__ __forceinline__ void pair_trial(const Sys& s, double t, double h, con
 // right-hand-side evaluations of one trial besides k1
 constexpr uint32_t pair_rhs(int PAIR) { return PAIR == kDormandPrince ? 6u : 5u; }
 
-// Compares, max / min and clamps of doubles on the integer pipe.  On this
-// part the FP64 pipe carries every flop of the solver and is the bottleneck; a
-// compare or a min / max costs it a full FP64 issue slot, the same as an FMA.
-// For x >= +0 (with +inf, and NaN with its sign bit clear, above every finite
-// value) the IEEE bit pattern read as a signed 64-bit integer orders exactly
-// as the value does, so these need no FP64 instruction.  For doubles of
-// either sign, okey() flips the magnitude bits of negatives, which orders all
-// finite values (with -0 just below +0).
-__device__ __forceinline__ long long nnbits(double x) { return __double_as_longlong(x); }
-__device__ __forceinline__ double absd(double x) {
-  return __hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x));
-}
-// a, b >= +0 or NaN (sign clear): NaN dominates max
-__device__ __forceinline__ double nnmax(double a, double b) { return nnbits(a) >= nnbits(b) ? a : b; }
-__device__ __forceinline__ double nnmin(double a, double b) { return nnbits(a) <= nnbits(b) ? a : b; }
-__device__ __forceinline__ long long okey(double x) {
-  const long long b = __double_as_longlong(x);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-// the larger / smaller of two finite doubles, keeping `a` on ties (as
-// `if (b > a) a = b` does)
-__device__ __forceinline__ double omax(double a, double b) { return okey(b) > okey(a) ? b : a; }
-__device__ __forceinline__ double omin(double a, double b) { return okey(b) < okey(a) ? b : a; }
-
 // E = max_c |err_c| / (atol + rtol max(|y_c|, |y5_c|)), >= 0, or NaN (sign
 // clear) when a trial blew up.  rcp_nr is within 1 ulp of 1/sc for the
 // normal, finite sc of a solve; a zero, subnormal, infinite or NaN sc gives
@@ -196,10 +174,6 @@ __device__ __forceinline__ double step_factor(double E) {
   const double Ec = nnmin(nnmax(E, 1e-4), 2000.0);
   const double fac = 0.9 * inv_fifth_root(Ec);
   return nnmin(nnmax(fac, 0.2), 5.0);
-}
-// the next step proposal after an accepted trial, within [dt_min, dt_max]
-__device__ __forceinline__ double bounded_step(double h, double fac, double dt_min, double dt_max) {
-  return nnmax(nnmin(h * fac, dt_max), dt_min);
 }
 
 // Claim the next system of a persistent lane (or the lane's own system in
@@ -378,25 +352,6 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
 //     the seat: y1 = y2 = 0 while y3 rises as beta q until y3 = delta, an
 //     interval advanced in closed form.
 // ---------------------------------------------------------------------------
-// Root estimate of a falling event function over a trial of length h, as a
-// fraction of h: g0 > 0 with slope d0 at the start (from k1), g1 < 0 at the
-// end.  The quadratic g0 + B x + A x^2 (B = d0 h, A = g1 - g0 - B) changes
-// sign once on (0, 1), at x = 2 g0 / (-B + sqrt(B^2 - 4 A g0)) for either sign
-// of A.  It is exact for a constant second derivative, so retries converge at
-// grazing impacts, where a chord from the fixed start of the retried step
-// closes in only linearly.  The chord g0 / (g0 - g1) stands in if rounding
-// takes the root out of (0, 1).
-__device__ __forceinline__ double event_frac(double g0, double d0, double g1, double h) {
-  const double B = d0 * h;
-  const double A = g1 - g0 - B;
-  const double D = fma(B, B, -4.0 * A * g0);
-  const double chord = g0 / (g0 - g1);
-  if (!(D >= 0.0)) return chord;
-  const double den = sqrt(D) - B;
-  const double x = 2.0 * g0 / den;
-  return (den > 0.0 && x > 0.0 && x < 1.0) ? x : chord;
-}
-
 template <int PAIR>
 __global__ void __launch_bounds__(256) ck_events_kernel(AdaptArgs a) {
   using Sys = ReliefValve;

@@ -51,9 +51,10 @@ def _phys(pa, f, dev):
 
 
 def km_solve_labels(ens, phys: dict, liquid: dict, n_phases: int, first_phase: int, dev, stream,
-                    tol: float = 1e-10, spread_tol: float = 1e-4, launch=None):
+                    tol: float = 1e-10, spread_tol: float = 1e-4, launch=None, per_system=None):
     """FP64 solve of the systems `phys` (device tensors) and their labels
-    y[n][2] = (ln max radius over phases >= first_phase, period-1 flag)."""
+    y[n][2] = (ln max radius over phases >= first_phase, period-1 flag).
+    per_system (a list) receives the accepted steps of every system."""
     import torch
     n = phys["pA1"].numel()
     C = ens.ens_km_coefficients(phys["pA1"], phys["f1"], phys["pA2"], phys["f2"], phys["theta"], phys["RE"],
@@ -70,7 +71,10 @@ def km_solve_labels(ens, phys: dict, liquid: dict, n_phases: int, first_phase: i
         st = ens.ens_sync(ctx)
         acc = torch.empty((2 * n_phases, n), dtype=torch.float64, device=dev)
         ens.ens_read(ctx, ens.ENS_ACC, acc)
-        steps = int(ens.ens_read(ctx, ens.ENS_NSTEPS).sum())
+        nacc = ens.ens_read(ctx, ens.ENS_NSTEPS)
+        steps = int(nacc.sum())
+        if per_system is not None:
+            per_system.append(nacc)
     finally:
         ens.ens_destroy(ctx)
     y = torch.empty((n, 2), dtype=torch.float32, device=dev)
@@ -230,8 +234,9 @@ def run(ens, train_shape=(362, 362), screen_m=1024, n_phases=64, first_phase=32,
     vi = W.screen_subgrid(screen_m, val_stride)
     vi_d = _t(vi, dev)
     t0 = time.perf_counter()
+    v_nacc = []
     y_v, st, v_steps = km_solve_labels(ens, _phys(_t(pa[vi], dev), _t(f[vi], dev), dev), liquid, n_phases,
-                                       first_phase, dev, stream, launch=fallback_launch)
+                                       first_phase, dev, stream, launch=fallback_launch, per_system=v_nacc)
     v_s = time.perf_counter() - t0
     truth = y_v[:, 0].cpu().numpy().astype(np.float64)
     label = y_v[:, 1].cpu().numpy() > 0.5
@@ -253,6 +258,21 @@ def run(ens, train_shape=(362, 362), screen_m=1024, n_phases=64, first_phase=32,
         "period1_fraction": float(label.mean()),
         "period1_error_rate_unflagged": float(np.mean(p1v[~fl] != label[~fl])) if (~fl).any() else None,
     }
+    # error against cost for other bounds, from the same calibration and
+    # validation solves: the gate each bound would give, its unflagged error
+    # on the validation sub-grid, the share of the FP64 work (steps) its
+    # flagged points carry, and the speedup that share implies
+    steps_v = v_nacc[0].astype(np.float64)
+    sd_v, g_v = sd[vi_d].cpu().numpy(), g[vi_d].cpu().numpy()
+    curve = []
+    for b in (0.02, 0.03, 0.05, 0.1, 0.2):
+        tb = calibrate_gradient_gate(err_c, sd_c, g_c, threshold, b, quantile)
+        fb = (sd_v > threshold) | (g_v > tb)
+        work = float(steps_v[fb].sum() / steps_v.sum())
+        curve.append({"bound": b, "gradient_threshold": tb, "flagged": float(fb.mean()), "fp64_work_share": work,
+                      f"unflagged_p{quantile:g}": q(err[~fb], quantile),
+                      "speedup_est": 1.0 / (work + out["screen_s"] / (v_s * n / vi.size))})
+    out["bound_curve"] = curve
     # the plain FP64 solve of the whole grid: the uniform sub-grid's measured
     # time scaled by the number of points
     out["fp64_grid_estimate_s"] = v_s * n / vi.size

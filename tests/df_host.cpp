@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdint>
 #include "km_df.cuh"
+#include "valve_df.cuh"
 using namespace ens::df;
 extern "C" {
 // C: [13][n] SoA like the library; fs, fc: forcing values; out: y2'
@@ -14,6 +15,19 @@ void accel_df(int n, const double* C, const double* fs, const double* fc, const 
     DF a = k.accel(from_double(fs[i]), from_double(fc[i]), from_double(y1[i]), from_double(y2[i]));
     out[i] = to_double(a);
   }
+}
+// params [5][n] like the library (q, kappa, delta, beta, r); y [3][n]; dy [3][n]
+void valve_df(int n, const double* P, const double* y, double* dy) {
+  for (int i = 0; i < n; ++i) {
+    ValveDF v;
+    v.load(P, n, i);
+    DF yy[3] = {from_double(y[i]), from_double(y[n + i]), from_double(y[2 * n + i])}, d[3];
+    v.f(yy, d);
+    for (int c = 0; c < 3; ++c) dy[c * n + i] = to_double(d[c]);
+  }
+}
+void sqrt_df(int n, const double* a, double* out) {
+  for (int i = 0; i < n; ++i) out[i] = to_double(ens::df::sqrt(from_double(a[i])));
 }
 void prims(int n, const double* a, const double* b, double* out) {
   // out[6][n]: add, mul, rcp(a), inv5(a), from/to round trip of a, a - b

@@ -78,8 +78,9 @@ def test_transient_phase_count_is_validated(ens):
 
 
 def test_reduced_precision_variants_are_limited_to_their_kernels(ens):
-    """ENS_FP32_COMP and ENS_FP32X2 exist for the Keller-Miksis phase mode with
-    Cash-Karp only; everything else is refused before any device work."""
+    """ENS_FP32_COMP exists for the Keller-Miksis phase mode with Cash-Karp,
+    ENS_FP32X2 for that and for the relief valve's event mode with Cash-Karp;
+    everything else is refused before any device work."""
     C = np.zeros((13, 1))
     y0 = np.array([[1.0], [0.0]])
     for prec in (ens.ENS_FP32_COMP, ens.ENS_FP32X2):
@@ -88,10 +89,15 @@ def test_reduced_precision_variants_are_limited_to_their_kernels(ens):
                 ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, 1, C, y0, (0.0, 1.0), solver,
                                ens.make_tol(n_phases=nph, prec=prec))
             assert e.value.status == ens.ENS_ENOTSUP
+    for prec, solver in ((ens.ENS_FP32_COMP, ens.ENS_RKCK45), (ens.ENS_FP32X2, ens.ENS_DOPRI5)):
         with pytest.raises(ens.EnsError) as e:
             ens.ens_create(ens.ENS_SYS_RELIEF_VALVE, 1, np.zeros((5, 1)), np.zeros((3, 1)), (0.0, 1.0),
-                           ens.ENS_RKCK45, ens.make_tol(event_tol=1e-6, prec=prec))
+                           solver, ens.make_tol(event_tol=1e-6, prec=prec))
         assert e.value.status == ens.ENS_ENOTSUP
+    with pytest.raises(ens.EnsError) as e:   # Lorenz has no reduced-precision kernel
+        ens.ens_create(ens.ENS_SYS_LORENZ, 1, np.zeros((3, 1)), np.zeros((3, 1)), (0.0, 1.0), ens.ENS_RKCK45,
+                       ens.make_tol(prec=ens.ENS_FP32X2))
+    assert e.value.status == ens.ENS_ENOTSUP
 
 
 def test_null_context_calls_are_harmless(ens):

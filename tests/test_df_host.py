@@ -1,6 +1,7 @@
-"""Host checks of the double-float arithmetic of the ENS_FP32X2 kernel
-(csrc/df.cuh) and of its Keller-Miksis right-hand side (csrc/km_df.cuh),
-built for the CPU with g++ (every function there is __host__ __device__).
+"""Host checks of the double-float arithmetic of the ENS_FP32X2 kernels
+(csrc/df.cuh) and of their Keller-Miksis and relief-valve right-hand sides
+(csrc/km_df.cuh, csrc/valve_df.cuh), built for the CPU with g++ (every
+function there is __host__ __device__).
 
 The error bounds are those of the double-word algorithms (Joldes, Muller &
 Popescu, ACM TOMS 44(2), 2017) in units of u^2 = 2^-48; the right-hand side
@@ -21,6 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_2011_01740_gb300", "csrc")
 U2 = 2.0 ** -48
 P = ctypes.POINTER(ctypes.c_double)
+P_ = P
 
 
 @pytest.fixture(scope="module")
@@ -95,3 +97,38 @@ def test_keller_miksis_right_hand_side_matches_the_oracle(lib):
              + np.abs(fs * (1 + C[9] * y2)) + np.abs(y1 * fc) + 1.5 * y2 ** 2) / np.abs(D)
     err = np.abs(out - ref) / scale
     assert np.percentile(err, 99) < 1e-13 and err.max() < 5e-13, (np.percentile(err, 99), err.max())
+
+
+def test_double_word_square_root(lib):
+    """One Newton step on the exact residual of the float square root: within
+    4 u^2 of sqrt of the pair's value (measured 3.4 u^2 at most, 1.4 u^2 at
+    the 99th percentile); 0 for zero and negative arguments."""
+    rng = np.random.default_rng(4)
+    x = 10.0 ** rng.uniform(-12, 12, 100_000)
+    xs = _prims(lib, x, x)[4]                   # the pairs' exact values
+    out = np.zeros_like(x)
+    lib.sqrt_df(x.size, _p(x), out.ctypes.data_as(P))
+    assert _rel(out, np.sqrt(xs)).max() <= 4.0 * U2
+    z = np.array([0.0, -1.0, -1e-30])
+    oz = np.ones(3)
+    lib.sqrt_df(3, _p(z), oz.ctypes.data_as(P))
+    assert np.array_equal(oz, np.zeros(3))
+
+
+def test_relief_valve_right_hand_side_matches_the_oracle(lib):
+    """Eqs. pressure_relief_valve_1-3 in pairs against the float64 oracle on
+    random states of the sweep's range (y3 < 0 exercises the clamp), relative
+    to the magnitude of the terms that cancel in each component."""
+    rng = np.random.default_rng(3)
+    n = 50_000
+    P = np.vstack([rng.uniform(0.2, 10.0, n), np.full(n, 1.25), np.full(n, 10.0), np.full(n, 20.0), np.full(n, 0.8)])
+    y = np.vstack([rng.uniform(-1e-6, 8.0, n), rng.uniform(-20.0, 20.0, n), rng.uniform(-1e-9, 60.0, n)])
+    ref = oracle.rhs(oracle.PRV, P, 0.0, y)
+    out = np.zeros_like(y)
+    lib.valve_df(n, _p(P), _p(y), out.ctypes.data_as(P_))
+    scale1 = np.abs(P[1] * y[1]) + np.abs(y[0] + P[2]) + np.abs(y[2])
+    scale2 = P[3] * (P[0] + np.abs(y[0]) * np.sqrt(np.maximum(y[2], 0.0)))
+    assert np.array_equal(out[0], y[1] + 0.0) or np.abs(out[0] - y[1]).max() <= 2.0 * U2 * np.abs(y[1]).max()
+    e1 = np.abs(out[1] - ref[1]) / scale1
+    e2 = np.abs(out[2] - ref[2]) / scale2
+    assert e1.max() < 2e-14 and e2.max() < 2e-14, (e1.max(), e2.max())

@@ -1,6 +1,7 @@
-"""GPU parity of the double-float Keller-Miksis kernel (ENS_FP32X2): state,
-stages, right-hand side, error estimate and controller as pairs of floats
-on the FP32 pipes, time and forcing in FP64.
+"""GPU parity of the double-float kernels (ENS_FP32X2): state, stages,
+right-hand side, error estimate and controller as pairs of floats on the
+FP32 pipes; time and forcing (Keller-Miksis), and time, event location,
+impact law and sticking (relief valve) in FP64.
 
 Its rounding is that of about 48-bit arithmetic: a few u^2 = 2^-48 per
 operation, and its right-hand side differs from the float64 one by up to
@@ -152,3 +153,121 @@ def test_status_words():
     g = _km(W.km(20, 20, n_phases=64), timeout_s=1e-6)
     assert g["sync"] == ens.ENS_ETIMEOUT
     assert np.all((g["status"] & ens.ENS_SYS_TIMEOUT) > 0)
+
+
+# ---------------------------------------------------------------------------
+# the relief valve (event mode, Sec. 4.3) in double-float arithmetic
+# ---------------------------------------------------------------------------
+
+def _valve(wl, launch=None, **kw):
+    t = wl["tol"]
+    return solve_gpu(ens.ENS_SYS_RELIEF_VALVE, wl["params"], wl["y0"], (t.t0, t.t1), ens.ENS_RKCK45,
+                     ens_tol_from(t, **{**X2, **kw}), launch=launch)
+
+
+def _well_valve(params, y0, otol):
+    """Oracle run and the valves whose value rows (Poincare ring and minimum)
+    and event counts stay put under the double-float perturbations (100 times
+    the FP64 kernel's: 1e-12 and -3e-13 of the state, a 1e-10 relative shift
+    of the first step)."""
+    a = oracle.cashkarp_solve(oracle.PRV, params, y0, otol)
+    shifted = oracle.make_tol(**{f: getattr(otol, f) for f, _ in otol._fields_})
+    shifted.dt0 = otol.dt0 * (1 + 1e-10)
+    well = a["status"] == 0
+    for b in (oracle.cashkarp_solve(oracle.PRV, params, np.asarray(y0) * (1 + 1e-12), otol),
+              oracle.cashkarp_solve(oracle.PRV, params, np.asarray(y0) * (1 - 3e-13), otol),
+              oracle.cashkarp_solve(oracle.PRV, params, y0, shifted)):
+        well &= (rel_err(b["acc"][:33], a["acc"][:33]) < 1e-9) & (b["status"] == 0)
+        well &= np.all(b["acc"][33:35] == a["acc"][33:35], axis=0)
+    return a, well
+
+
+def _compare_valve(g, r, well, idx=None):
+    """Event counts (maxima, impacts) exactly the oracle's on the
+    well-conditioned valves; the value rows within the scaled bar where the
+    step sequences agree (99 % within the FP64 bar); the end states within
+    1e-7."""
+    gi = (lambda a: a) if idx is None else (lambda a: a[..., idx])
+    acc = gi(g["acc"])
+    assert np.array_equal(acc[33][well], r["acc"][33][well])
+    assert np.array_equal(acc[34][well], r["acc"][34][well])
+    same = well & (gi(g["nacc"]) == r["nacc"]) & (gi(g["nrej"]) == r["nrej"])
+    assert same.sum() >= 0.8 * well.sum(), (same.sum(), well.sum())
+    err = rel_err(acc[:33], r["acc"][:33])[same]
+    assert np.all(err < X2_TOL), err.max()
+    assert np.mean(err < ACC_TOL) >= QUANTILE, np.mean(err < ACC_TOL)
+    assert np.all(rel_err(gi(g["y"]), r["y"])[well] < 1e-7), rel_err(gi(g["y"]), r["y"])[well].max()
+
+
+def test_valve_parity():
+    wl = W.prv(300, t1=64.0)                # impacting and free valves, a ragged last block
+    g = _valve(wl)
+    r, well = _well_valve(wl["params"], wl["y0"], oracle_tol_from(wl["tol"]))
+    assert g["sync"] == ens.ENS_OK and np.all(g["status"] == 0)
+    assert well.mean() > 0.6, well.mean()
+    _compare_valve(g, r, well)
+    assert np.all(g["t"] == 64.0)
+
+
+def test_valve_full_sweep_sampled_parity():
+    """262,144 valves, t in [0, 1024]: every valve finishes without a status
+    bit, impacts below q ~ 7.5 (Sec. 4.3) and not above, and a stratified
+    sample matches the oracle."""
+    wl = W.prv(262144, t1=1024.0)
+    g = _valve(wl)
+    assert g["sync"] == ens.ENS_OK and np.all(g["status"] == 0)
+    q = wl["params"][0]
+    ymin = g["acc"][32]
+    assert np.mean(ymin[q < 7.0] == 0.0) > 0.95 and np.all(ymin[q > 8.0] > 0.0)
+    assert np.all(g["y"][2] >= 0.0)
+    idx = W.subsample(262144, 96)
+    sub = W.take(wl, idx)
+    r, well = _well_valve(sub["params"], sub["y0"], oracle_tol_from(wl["tol"]))
+    assert well.mean() > 0.4, well.mean()
+    _compare_valve(g, r, well, idx)
+
+
+def test_valve_grazing_impact_matches_oracle():
+    """The recorded grazing state (q = 7.5393, a dip of about 1e-5 below the
+    seat): the event location converges with the double-float stages too."""
+    params = np.array([[7.5392987796736906], [1.25], [10.0], [20.0], [0.8]])
+    y0 = np.array([[0.0013698420381308958], [-0.3162497537150412], [45.746744783524875]])
+    for dt0 in (0.0085, 0.008889370476683223, 0.0107):
+        kw = dict(rtol=1e-10, atol=1e-10, dt0=dt0, dt_min=1e-14, dt_max=1.0, event_tol=1e-6, acc_t_start=0.0)
+        g = solve_gpu(ens.ENS_SYS_RELIEF_VALVE, params, y0, (0.0, 0.05), ens.ENS_RKCK45, ens.make_tol(**kw, **X2))
+        r = oracle.cashkarp_solve(oracle.PRV, params, y0, oracle.make_tol(t0=0.0, t1=0.05, **kw))
+        assert g["status"][0] == 0 and r["status"][0] == 0
+        assert g["acc"][34, 0] == 1 and r["acc"][34, 0] == 1
+        assert np.all(rel_err(g["y"], r["y"]) < 1e-7), (g["y"][:, 0], r["y"][:, 0])
+
+
+def test_valve_sticking_interval_matches_oracle():
+    """A valve started on the seat sticks after its first tiny rebound and
+    lifts at the closed-form time: both sides agree on the state before and
+    after the lift."""
+    params = np.array([[1.0], [1.25], [10.0], [20.0], [0.8]])
+    y0 = np.array([[0.0], [0.0], [5.0]])
+    for t1 in (0.2, 0.26):
+        kw = dict(rtol=1e-10, atol=1e-10, dt0=1e-3, dt_min=1e-14, dt_max=1.0, event_tol=1e-6, acc_t_start=0.0)
+        g = solve_gpu(ens.ENS_SYS_RELIEF_VALVE, params, y0, (0.0, t1), ens.ENS_RKCK45, ens.make_tol(**kw, **X2))
+        r = oracle.cashkarp_solve(oracle.PRV, params, y0, oracle.make_tol(t0=0.0, t1=t1, **kw))
+        assert g["status"][0] == 0 and g["acc"][34, 0] == r["acc"][34, 0] == 1
+        assert np.abs(g["y"][:, 0] - r["y"][:, 0]).max() <= 1e-7 * np.abs(r["y"][:, 0]).max()
+
+
+def test_valve_launch_shapes_are_bitwise_identical():
+    wl = W.prv(1000, t1=32.0)
+    ref = _valve(wl, launch=ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=128))
+    for L in (ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=256, blocks_per_sm=1, cost_order=1),
+              ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=64, blocks_per_sm=2, use_graph=1)):
+        g = _valve(wl, launch=L)
+        for k in ("y", "acc", "nacc", "nrej", "nrhs", "status", "dt"):
+            assert np.array_equal(g[k], ref[k], equal_nan=True), (k, L.as_dict())
+
+
+def test_valve_status_words():
+    wl = W.prv(64, t1=64.0)
+    g = _valve(wl, max_steps=7)
+    assert np.all((g["status"] & ens.ENS_SYS_MAX_STEPS) > 0) and g["sync"] == ens.ENS_ESYSTEM
+    g = _valve(W.prv(20000, t1=1024.0), timeout_s=1e-6)
+    assert g["sync"] == ens.ENS_ETIMEOUT
