@@ -10,7 +10,16 @@ from paper_2011_01740_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-BF16_TOL = 2e-2      # relative, per parameter block: BF16 operands (8-bit mantissa), FP32 accumulation
+BF16_TOL = 2e-2      # relative, per output: BF16 operands (8-bit mantissa), FP32 accumulation
+# Gradients, element by element: |g - g_ref| <= GRAD_TOL * max |g_ref| within
+# each parameter block (the 1e-2 bar for BF16 training), and the block's
+# 2-norm within GRAD_TOL as well.  Measured on these batches: at most 7.2e-3
+# (element-wise) and 9.2e-3 (norm) over W1..W5 and b1..b4.  The output bias
+# b5 (two entries) is the batch sum of the residuals out - y, which have
+# mixed signs: the ~0.5 % error of the BF16 forward outputs comes through that
+# cancellation amplified (1.3e-2 measured), so b5 takes 2e-2.
+GRAD_TOL = 1e-2
+GRAD_TOL_B5 = 2e-2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -100,11 +109,15 @@ def test_gradient_matches_oracle(n, impl):
     loss, grad = _loss_grad(p, x, y, impl)
     for k in range(M):
         L, g = omlp.grad(p[k].astype(np.float64), x.astype(np.float64), y.astype(np.float64))
-        assert abs(loss[k] - L) < BF16_TOL * abs(L), (k, loss[k], L)
+        assert abs(loss[k] - L) < 1e-3 * abs(L), (k, loss[k], L)
         for name, lo, hi in _blocks():
             ref = g[lo:hi]
-            err = np.linalg.norm(grad[k, lo:hi] - ref) / max(np.linalg.norm(ref), 1e-30)
-            assert err < BF16_TOL, (k, name, err)
+            tol = GRAD_TOL_B5 if name == "b5" else GRAD_TOL
+            scale = max(np.abs(ref).max(), 1e-30)
+            elem = np.abs(grad[k, lo:hi] - ref) / scale
+            assert elem.max() <= tol, (k, name, elem.max(), int(elem.argmax()))
+            norm = np.linalg.norm(grad[k, lo:hi] - ref) / max(np.linalg.norm(ref), 1e-30)
+            assert norm <= tol, (k, name, norm)
 
 
 @pytest.mark.parametrize("impl", [1, 0])
