@@ -73,6 +73,17 @@ __host__ __device__ __forceinline__ DF add(DF x, DF y) {
 }
 __host__ __device__ __forceinline__ DF sub(DF x, DF y) { return add(x, neg(y)); }
 
+// DW + DW in Dekker's form: the exact sum of the high parts plus the rounded
+// sum of the low parts and the rounding error, renormalised (11 flops).  Its
+// error is bounded in the operands' magnitude, |error| <= 2 u^2 (|x| + |y|),
+// not in the result's: enough for a sum of Runge-Kutta stage terms, whose
+// own conditioning is relative to the terms' magnitude (as FP64 arithmetic
+// rounds them), where the accurate add above keeps a relative bound of the
+// result even under cancellation.
+__host__ __device__ __forceinline__ DF add_terms(DF x, DF y) {
+  const DF s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
 // DW + FP (10 flops)
 __host__ __device__ __forceinline__ DF add(DF x, float y) {
   const DF s = two_sum(x.hi, y);
@@ -98,6 +109,8 @@ __host__ __device__ __forceinline__ DF mul(DF x, DF y) {
 
 // a b + c
 __host__ __device__ __forceinline__ DF fma(DF a, DF b, DF c) { return add(mul(a, b), c); }
+// a b + c with the sum in Dekker's form (20 flops against 29)
+__host__ __device__ __forceinline__ DF fma_terms(DF a, DF b, DF c) { return add_terms(mul(a, b), c); }
 
 // 1 / y: r0 = the correctly rounded float reciprocal of y.hi, then
 // r = r0 (1 + e + e^2) with the residual e = 1 - y r0 formed in double-word

@@ -290,7 +290,11 @@ __global__ void __launch_bounds__(256) ck_phased_df_kernel(AdaptArgs a) {
 // and retries with the step cut to the earliest estimated root (one half when
 // the impact starts inside the band, at most 40 retries); otherwise the step
 // is accepted and events are located at its end; a rebound whose apex stays
-// inside the band leaves the valve on the seat until y3 = delta.
+// inside the band leaves the valve on the seat until y3 = delta.  The sums of
+// stage terms and the error scale atol + rtol max(|y|, |y5|) take the
+// double-word addition in Dekker's form (error bounded in the terms'
+// magnitude, as FP64 rounding bounds them; the scale's terms are positive);
+// the state update y + h S takes the accurate form.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) ck_events_df_kernel(AdaptArgs a) {
   using namespace df;
@@ -400,21 +404,21 @@ __global__ void __launch_bounds__(256) ck_events_df_kernel(AdaptArgs a) {
       for (int c = 0; c < D; ++c) x[c] = add(y[c], mul(mul(A21, k1[c]), hd));
       s.f(x, k2);
 #pragma unroll
-      for (int c = 0; c < D; ++c) x[c] = add(y[c], mul(df::fma(A32, k2[c], mul(A31, k1[c])), hd));
+      for (int c = 0; c < D; ++c) x[c] = add(y[c], mul(fma_terms(A32, k2[c], mul(A31, k1[c])), hd));
       s.f(x, k3);
 #pragma unroll
       for (int c = 0; c < D; ++c)
-        x[c] = add(y[c], mul(df::fma(A43, k3[c], df::fma(A42, k2[c], mul(A41, k1[c]))), hd));
+        x[c] = add(y[c], mul(fma_terms(A43, k3[c], fma_terms(A42, k2[c], mul(A41, k1[c]))), hd));
       s.f(x, k4);
 #pragma unroll
       for (int c = 0; c < D; ++c)
         x[c] = add(y[c],
-                   mul(df::fma(A54, k4[c], df::fma(A53, k3[c], df::fma(A52, k2[c], mul(A51, k1[c])))), hd));
+                   mul(fma_terms(A54, k4[c], fma_terms(A53, k3[c], fma_terms(A52, k2[c], mul(A51, k1[c])))), hd));
       s.f(x, k5);
 #pragma unroll
       for (int c = 0; c < D; ++c)
-        x[c] = add(y[c], mul(df::fma(A65, k5[c],
-                                     df::fma(A64, k4[c], df::fma(A63, k3[c], df::fma(A62, k2[c], mul(A61, k1[c]))))),
+        x[c] = add(y[c], mul(fma_terms(A65, k5[c],
+                                     fma_terms(A64, k4[c], fma_terms(A63, k3[c], fma_terms(A62, k2[c], mul(A61, k1[c]))))),
                              hd));
       s.f(x, k6);
       nrhs += 5;
@@ -424,10 +428,10 @@ __global__ void __launch_bounds__(256) ck_events_df_kernel(AdaptArgs a) {
       bool nan = false;
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        n[c] = add(y[c], mul(df::fma(B6, k6[c], df::fma(B4, k4[c], df::fma(B3, k3[c], mul(B1, k1[c])))), hd));
-        const DF e = mul(df::fma(D6, k6[c], df::fma(D5, k5[c], df::fma(D4, k4[c], df::fma(D3, k3[c], mul(D1, k1[c]))))),
+        n[c] = add(y[c], mul(fma_terms(B6, k6[c], fma_terms(B4, k4[c], fma_terms(B3, k3[c], mul(B1, k1[c])))), hd));
+        const DF e = mul(fma_terms(D6, k6[c], fma_terms(D5, k5[c], fma_terms(D4, k4[c], fma_terms(D3, k3[c], mul(D1, k1[c]))))),
                          hd);
-        const DF sc = df::fma(rtol, dmax(dabs(y[c]), dabs(n[c])), atol);
+        const DF sc = fma_terms(rtol, dmax(dabs(y[c]), dabs(n[c])), atol);
         const DF r = mul(dabs(e), rcp(sc));
         nan |= isnan(r.hi) || isnan(n[c].hi);
         E = dmax(E, r);

@@ -26,6 +26,9 @@ void valve_df(int n, const double* P, const double* y, double* dy) {
     for (int c = 0; c < 3; ++c) dy[c * n + i] = to_double(d[c]);
   }
 }
+void add_terms_df(int n, const double* a, const double* b, double* out) {
+  for (int i = 0; i < n; ++i) out[i] = to_double(add_terms(from_double(a[i]), from_double(b[i])));
+}
 void sqrt_df(int n, const double* a, double* out) {
   for (int i = 0; i < n; ++i) out[i] = to_double(ens::df::sqrt(from_double(a[i])));
 }

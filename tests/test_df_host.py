@@ -132,3 +132,18 @@ def test_relief_valve_right_hand_side_matches_the_oracle(lib):
     e1 = np.abs(out[1] - ref[1]) / scale1
     e2 = np.abs(out[2] - ref[2]) / scale2
     assert e1.max() < 2e-14 and e2.max() < 2e-14, (e1.max(), e2.max())
+
+
+def test_dekker_addition_error_is_bounded_by_the_operands(lib):
+    """add_terms (stage sums): |error| <= 2 u^2 (|x| + |y|), also when the sum
+    cancels (y near -x)."""
+    rng = np.random.default_rng(6)
+    n = 100_000
+    a = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-6, 6, n)
+    b = np.where(rng.uniform(size=n) < 0.5, -a * (1 + rng.uniform(-1e-6, 1e-6, n)),
+                 rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-6, 6, n))
+    xa, xb = _prims(lib, a, b)[4], _prims(lib, b, a)[4]
+    out = np.zeros(n)
+    lib.add_terms_df(n, _p(a), _p(b), out.ctypes.data_as(P))
+    err = np.abs(out - (xa + xb)) / (np.abs(xa) + np.abs(xb))
+    assert err.max() <= 2.0 * U2, err.max() / U2
