@@ -161,7 +161,22 @@ def _as_f64(x):
     return np.ascontiguousarray(x, dtype=np.float64)
 
 
-def _stream(stream):
+def _stream(stream, keep=None):
+    """The raw stream handle.  With `keep` (the arrays of a call), every CUDA
+    tensor among them is marked as used by that stream (record_stream), so
+    that PyTorch's caching allocator does not hand its memory to another
+    tensor while the asynchronous work queued here may still read or write
+    it -- also when the caller drops its last reference right after the call
+    (a temporary argument)."""
+    if keep and stream is not None:
+        try:
+            import torch
+            ts = stream if isinstance(stream, torch.cuda.Stream) else torch.cuda.ExternalStream(int(stream))
+            for t in keep:
+                if isinstance(t, torch.Tensor) and t.is_cuda:
+                    t.record_stream(ts)
+        except ImportError:
+            pass
     if stream is None:
         try:
             import torch
@@ -218,7 +233,7 @@ def ens_set_inputs(ctx: int, params=None, y0=None, stream=None):
     keep = []
     params = None if params is None else _as_f64(params)
     y0 = None if y0 is None else _as_f64(y0)
-    _check(lib().ens_set_inputs(ctx, _ptr(params, keep), _ptr(y0, keep), _stream(stream)), ctx)
+    _check(lib().ens_set_inputs(ctx, _ptr(params, keep), _ptr(y0, keep), _stream(stream, keep)), ctx)
 
 
 def ens_set_launch(ctx: int, cfg: EnsLaunch | None):
@@ -318,7 +333,7 @@ def ens_eval_rhs(sys: int, n: int, params, t, y, dy, stream=None):
         L._rhs_bound = True
     keep = []
     _check(L.ens_eval_rhs(int(sys), int(n), _ptr(params, keep), _ptr(t, keep), _ptr(y, keep), _ptr(dy, keep),
-                          _stream(stream)), None)
+                          _stream(stream, keep)), None)
     return dy
 
 
@@ -338,7 +353,7 @@ def ens_solve_noalloc(sys: int, n: int, params, y0, t_span, tol: EnsTol, y, t_ou
     ptrs = [_ptr(a, keep) for a in (params, y0)]
     outs = [_ptr(a, keep) for a in (y, t_out, dt_out, acc, status, nacc, nrej, nrhs)]
     _check(L.ens_solve_noalloc(int(sys), int(n), *ptrs, ts, ctypes.byref(tol), *outs, int(cost_order),
-                               _stream(stream)), None)
+                               _stream(stream, keep)), None)
 
 
 def ens_last_error(ctx: int | None = None) -> str:
@@ -364,7 +379,7 @@ def ens_km_coefficients(pA1, f1, pA2, f2, theta, RE, liquid: dict, out=None, str
     keep = []
     liq = EnsLiquid(*[float(liquid[k]) for k in ("rho", "c", "mu", "sigma", "pv", "pinf", "gamma")])
     st = lib().ens_km_coefficients(n, *[_ptr(a, keep) for a in arrs], ctypes.byref(liq),
-                                   _ptr(out, keep), _stream(stream))
+                                   _ptr(out, keep), _stream(stream, keep))
     _check(st, None)
     return out
 
@@ -468,7 +483,7 @@ def ens_mlp_get_params(m: int, params):
 
 def ens_mlp_forward(m: int, n: int, x, out, stream=None):
     keep = []
-    _mcheck(_mlp_lib().ens_mlp_forward(m, int(n), _ptr(x, keep), _ptr(out, keep), _stream(stream)), m)
+    _mcheck(_mlp_lib().ens_mlp_forward(m, int(n), _ptr(x, keep), _ptr(out, keep), _stream(stream, keep)), m)
     return out
 
 
@@ -476,7 +491,7 @@ def ens_mlp_loss_grad(m: int, n: int, x, y, members: int, grad, stream=None):
     keep = []
     loss = (ctypes.c_float * members)()
     _mcheck(_mlp_lib().ens_mlp_loss_grad(m, int(n), _ptr(x, keep), _ptr(y, keep), ctypes.cast(loss, ctypes.c_void_p),
-                                         _ptr(grad, keep), _stream(stream)), m)
+                                         _ptr(grad, keep), _stream(stream, keep)), m)
     return np.array(list(loss), dtype=np.float32)
 
 
@@ -484,14 +499,14 @@ def ens_mlp_train(m: int, n: int, x, y, cfg: EnsTrainCfg, members: int, stream=N
     keep = []
     hist = np.zeros((max(cfg.epochs, 1), members), dtype=np.float32)
     _mcheck(_mlp_lib().ens_mlp_train(m, int(n), _ptr(x, keep), _ptr(y, keep), ctypes.byref(cfg),
-                                     hist.ctypes.data, _stream(stream)), m)
+                                     hist.ctypes.data, _stream(stream, keep)), m)
     return hist[: cfg.epochs]
 
 
 def ens_mlp_screen(m: int, n: int, x, mean, stdv, p1, stream=None):
     keep = []
     _mcheck(_mlp_lib().ens_mlp_screen(m, int(n), _ptr(x, keep), _ptr(mean, keep), _ptr(stdv, keep), _ptr(p1, keep),
-                                      _stream(stream)), m)
+                                      _stream(stream, keep)), m)
 
 
 def ens_mlp_set_screen_impl(m: int, impl: int) -> int:
@@ -533,14 +548,14 @@ def ens_mlp_destroy(m: int):
 def ens_km_features(n: int, pA, f, rng, x, stream=None):
     keep = []
     r = (ctypes.c_double * 4)(*[float(v) for v in rng])
-    _mcheck(_mlp_lib().ens_km_features(int(n), _ptr(pA, keep), _ptr(f, keep), r, _ptr(x, keep), _stream(stream)))
+    _mcheck(_mlp_lib().ens_km_features(int(n), _ptr(pA, keep), _ptr(f, keep), r, _ptr(x, keep), _stream(stream, keep)))
     return x
 
 
 def ens_km_labels(n: int, acc, n_phases: int, first_phase: int, spread_tol: float, y, stream=None):
     keep = []
     _mcheck(_mlp_lib().ens_km_labels(int(n), _ptr(acc, keep), int(n_phases), int(first_phase), float(spread_tol),
-                                     _ptr(y, keep), _stream(stream)))
+                                     _ptr(y, keep), _stream(stream, keep)))
     return y
 
 
@@ -549,28 +564,28 @@ def ens_select_gate(n: int, v, thr: float, w, thr_w: float, idx, stream=None) ->
     keep = []
     cnt = ctypes.c_int64(0)
     _mcheck(_mlp_lib().ens_select_gate(int(n), _ptr(v, keep), float(thr), _ptr(w, keep), float(thr_w),
-                                       _ptr(idx, keep), ctypes.byref(cnt), _stream(stream)))
+                                       _ptr(idx, keep), ctypes.byref(cnt), _stream(stream, keep)))
     return int(cnt.value)
 
 
 def ens_grid_gradient(rows: int, cols: int, stride: int, v, d_row: float, d_col: float, g, stream=None):
     keep = []
     _mcheck(_mlp_lib().ens_grid_gradient(int(rows), int(cols), int(stride), _ptr(v, keep), float(d_row),
-                                         float(d_col), _ptr(g, keep), _stream(stream)))
+                                         float(d_col), _ptr(g, keep), _stream(stream, keep)))
     return g
 
 
 def ens_feature_stencil(n: int, x, d0: float, d1: float, out, stream=None):
     keep = []
     _mcheck(_mlp_lib().ens_feature_stencil(int(n), _ptr(x, keep), float(d0), float(d1), _ptr(out, keep),
-                                           _stream(stream)))
+                                           _stream(stream, keep)))
     return out
 
 
 def ens_stencil_gradient(n: int, v, d0: float, d1: float, g, stream=None):
     keep = []
     _mcheck(_mlp_lib().ens_stencil_gradient(int(n), _ptr(v, keep), float(d0), float(d1), _ptr(g, keep),
-                                            _stream(stream)))
+                                            _stream(stream, keep)))
     return g
 
 
@@ -578,17 +593,17 @@ def ens_select_above(n: int, v, thr: float, idx, stream=None) -> int:
     keep = []
     cnt = ctypes.c_int64(0)
     _mcheck(_mlp_lib().ens_select_above(int(n), _ptr(v, keep), float(thr), _ptr(idx, keep), ctypes.byref(cnt),
-                                        _stream(stream)))
+                                        _stream(stream, keep)))
     return int(cnt.value)
 
 
 def ens_gather_f64(k: int, idx, src, dst, stream=None):
     keep = []
-    _mcheck(_mlp_lib().ens_gather_f64(int(k), _ptr(idx, keep), _ptr(src, keep), _ptr(dst, keep), _stream(stream)))
+    _mcheck(_mlp_lib().ens_gather_f64(int(k), _ptr(idx, keep), _ptr(src, keep), _ptr(dst, keep), _stream(stream, keep)))
     return dst
 
 
 def ens_scatter_labels(k: int, idx, y, dst, stream=None):
     keep = []
-    _mcheck(_mlp_lib().ens_scatter_labels(int(k), _ptr(idx, keep), _ptr(y, keep), _ptr(dst, keep), _stream(stream)))
+    _mcheck(_mlp_lib().ens_scatter_labels(int(k), _ptr(idx, keep), _ptr(y, keep), _ptr(dst, keep), _stream(stream, keep)))
     return dst
