@@ -34,14 +34,14 @@ from paper_2011_01740_gb300 import workloads as W  # noqa: E402
 # the Keller-Miksis kernel, and per RK4 step of the x' = x^2 - p and Lorenz
 # kernels, from the ncu instruction counters of profiles/ (None until
 # measured: the roofline then reports achieved = null).
-FLOPS_PER_KM_TRIAL = 604.90  # 237.61 DFMA + 121.70 DMUL + 7.98 DADD per trial (profiles/)
+FLOPS_PER_KM_TRIAL = 589.91  # 232.61 DFMA + 121.70 DMUL + 2.98 DADD per trial (profiles/)
 # all FP64 thread instructions per trial (DFMA, DMUL, DADD, compares, min/max),
 # for the FP64 pipe's instruction-issue fraction
-FP64_INST_PER_KM_TRIAL = 367.29
+FP64_INST_PER_KM_TRIAL = 357.29
 # DRAM bytes (read + write) of one benchmarked Keller-Miksis launch, from the
 # one-pass ncu capture in profiles/ (inputs 15.7 MB read once, 134 MB of
 # per-period accessories written once); None once the kernel changes.
-KM_LAUNCH_DRAM_BYTES = 37893888 + 120424704
+KM_LAUNCH_DRAM_BYTES = 33905152 + 116558592
 FLOPS_PER_X2P_STEP = 21.0     # 10 DFMA + 1 DADD (Sec. 3.2.2 counters; kernel counted by ncu)
 FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast kernel
 # executed flops per trial of the other adaptive kernels (ncu counts,
@@ -49,6 +49,7 @@ FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast k
 FLOPS_PER_VALVE_TRIAL = 301.59        # FP64: 115.0 DFMA + 57.5 DMUL + 14.1 DADD, ck_events_kernel
 FLOPS_FP32_PER_FP32C_TRIAL = 1516.0   # FP32: 441.1 FFMA + 162.4 FMUL + 471.4 FADD, ck_phased_fp32c_kernel
 FLOPS_FP32_PER_DF_TRIAL = 5277.6      # FP32: 746.1 FFMA + 454.9 FMUL + 3330.5 FADD, ck_phased_df_kernel
+FLOPS_FP32_PER_DF_VALVE_TRIAL = 3173.5  # FP32, ck_events_df_kernel
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK = 152 * 128 * 2.0 * 2070.0e6
 
@@ -342,6 +343,14 @@ def km_roofline(trials: float, kernel_ms: float, accepted: float) -> dict:
             "useful_frac": accepted / trials if trials else None}
 
 
+def _tune_table(ens, ctx):
+    """The context's last tuning: [mode, block, blocks_per_sm, cost_order,
+    systems_per_thread, ms, horizon fraction] per candidate."""
+    return [[r["launch"]["mode"], r["launch"]["block"], r["launch"]["blocks_per_sm"], r["launch"]["cost_order"],
+             r["launch"]["systems_per_thread"], round(r["ms"], 3), r["horizon_frac"]]
+            for r in ens.ens_autotune_table(ctx)]
+
+
 def _r(x, digits=4):
     """Round to `digits` significant digits (None passes through)."""
     if x is None:
@@ -387,7 +396,8 @@ def configs_summary(value, roofline, sec, n_headline):
         out["c3_valve_262144_fp64"] = {"value": _r(v["value"]), "s": _r(v["ms"] / 1e3), "frac": _r(v.get("fp64_frac"), 3),
                                        "launch": _shape(v["launch"]), "parity": "events exact, acc <=1e-8"}
         if v.get("fp32x2"):
-            out["c3_valve_262144_fp64"]["df"] = _r({k: v["fp32x2"][k] for k in ("s", "speedup", "err_p99")}, 3)
+            out["c3_valve_262144_fp64"]["df"] = _r({k: v["fp32x2"][k] for k in ("s", "speedup", "err_p99", "fp32_frac")},
+                                                   3)
     c4 = sec.get("km_1024x1024_precisions")
     if c4:
         names = (("fp64_1e-10", "fp64_tol1e-10"), ("fp64_1e-8", "fp64_tol1e-8"), ("fp32c_1e-8", "fp32c_tol1e-8"),
@@ -822,11 +832,12 @@ def run_secondary(ens, torch, stream, dev, tuned=True):
                              ens.make_tol(dt0=wl["dt"], n_steps=wl["nsteps"]))
         ens.ens_set_launch(ctx, ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=32))
         best = ens.ens_autotune(ctx, stream) if tuned else ens.ens_get_launch(ctx)
+        table = _tune_table(ens, ctx) if tuned else None
         ms = timed(ctx, 20 if N <= 65536 else 5)
         ens.ens_destroy(ctx)
         sps = N * 1000 / (ms / 1e3)
         sweep[N] = {"ms": ms, "value": sps, "unit": "system-steps/s",
-                    "fp64_frac": sps * FLOPS_PER_LORENZ_STEP / FP64_PEAK, "launch": best.as_dict()}
+                    "fp64_frac": sps * FLOPS_PER_LORENZ_STEP / FP64_PEAK, "launch": best.as_dict(), "tune_table": table}
     out["lorenz_rk4_16384"] = sweep[16384]
     out["lorenz_rk4_n_sweep"] = sweep
     # relief valve, 262144 systems, t in [0, 1024], events
@@ -844,6 +855,7 @@ def run_secondary(ens, torch, stream, dev, tuned=True):
         ens.ens_autotune(ctx, stream)
         tune_s = time.perf_counter() - t0
     L = ens.ens_get_launch(ctx)
+    valve_table = _tune_table(ens, ctx) if tuned else None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     ens.ens_solve(ctx, stream)
@@ -859,6 +871,7 @@ def run_secondary(ens, torch, stream, dev, tuned=True):
     trials = float(nacc.sum() + nrej.sum())
     out["relief_valve_262144"] = {"ms": ms, "kernel_ms": kms, "status": st, "value": float(nacc.sum()) / (ms / 1e3),
                                   "unit": "system-steps/s", "trials": trials, "launch": L.as_dict(), "tune_s": tune_s,
+                                  "tune_table": valve_table,
                                   "fp64_frac": (FLOPS_PER_VALVE_TRIAL * trials / (kms / 1e3) / FP64_PEAK
                                                 if FLOPS_PER_VALVE_TRIAL else None)}
     # the same sweep in double-float arithmetic (state, stages, right-hand
@@ -882,6 +895,7 @@ def run_secondary(ens, torch, stream, dev, tuned=True):
     ms2 = e0.elapsed_time(e1)
     kms2 = ens.ens_kernel_ms(ctx)
     nacc2 = ens.ens_read(ctx, ens.ENS_NSTEPS)
+    nrej2 = ens.ens_read(ctx, ens.ENS_NREJ)
     acc2 = torch.empty((35, 262144), dtype=torch.float64, device=dev)
     ens.ens_read(ctx, ens.ENS_ACC, acc2)
     ens.ens_destroy(ctx)
@@ -890,9 +904,11 @@ def run_secondary(ens, torch, stream, dev, tuned=True):
     d = torch.where(torch.isnan(acc2[:33]) & torch.isnan(acc64[:33]), torch.zeros_like(d), d)
     rel = (d.amax(dim=0) / acc64[:33].abs().nan_to_num(0.0).amax(dim=0).clamp_min(1e-300))[same_events]
     q = _quantiles(rel, torch)
+    trials2 = float(nacc2.sum() + nrej2.sum())
     out["relief_valve_262144"]["fp32x2"] = {
         "ms": ms2, "kernel_ms": kms2, "s": ms2 / 1e3, "status": st2, "value": float(nacc2.sum()) / (ms2 / 1e3),
         "speedup": ms / ms2, "launch": L2.as_dict(), "tune_s": tune2,
+        "fp32_frac": FLOPS_FP32_PER_DF_VALVE_TRIAL * trials2 / (kms2 / 1e3) / FP32_PEAK,
         "same_event_counts": float(same_events.double().mean()),
         "value_rows_rel_diff_vs_fp64": q, "err_p99": q["p99"]}
     return out
@@ -992,6 +1008,19 @@ def run_profile_case(case: str):
         ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
                              ens.ENS_RKCK45, tol)
         ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=2, cost_order=0))
+    elif case == "km_pow":
+        # the 362 x 362 sweep with gamma = 1.33 (C10 = 3.99 is not 21/5): the
+        # general-exponent kernel, whose right-hand side calls pow(); 2 periods
+        km = km_slice(1, 0, n_phases=2)
+        ph = km["phys"]
+        liquid = dict(km["liquid"], gamma=1.33)
+        C = ens.ens_km_coefficients(ph["pA1"], ph["f1"], ph["pA2"], ph["f2"], ph["theta"], ph["RE"], liquid)
+        t = km["tol"]
+        tol = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max,
+                           n_phases=t.n_phases, phase_len=t.phase_len)
+        ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
+                             ens.ENS_RKCK45, tol)
+        ens.ens_set_launch(ctx, ens.make_launch(block=160, blocks_per_sm=1, cost_order=0))
     elif case == "km_full64":
         # the benchmarked launch (all systems, 64 periods, longest-first claiming)
         km = km_slice(1, 0, n_phases=64)
@@ -1099,11 +1128,74 @@ def run_profile_case(case: str):
     ens.ens_destroy(ctx)
 
 
+def run_probe(case: str):
+    """Timing probes behind the launch-shape reasoning (one JSON line each):
+    pipe_sharing -- copies of the 362 x 362 sweep's longest Keller-Miksis
+    system at controlled occupancy (1 to 8 warps on one SM, 4 and 5 warps on
+    every SM; 16 periods), the main kernel's time per trial;
+    trial_distribution -- trials per system of the full sweep (64 periods) and
+    of its one-phase pilot: quantiles, the share of the longest systems, the
+    pilot's rank correlation with the full count."""
+    import torch
+    import paper_2011_01740_gb300 as ens
+    torch.cuda.set_device(0)
+    km = km_slice(1, 0, n_phases=64)
+    ph = km["phys"]
+    t = km["tol"]
+    C = ens.ens_km_coefficients(ph["pA1"], ph["f1"], ph["pA2"], ph["f2"], ph["theta"], ph["RE"], km["liquid"])
+
+    def solve(Cs, y0, nph, launch):
+        tol = ens.make_tol(rtol=t.rtol, atol=t.atol, dt0=t.dt0, dt_min=t.dt_min, dt_max=t.dt_max, n_phases=nph,
+                           timeout_s=900.0)
+        ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, Cs.shape[1], Cs, y0, (0.0, 1.0), ens.ENS_RKCK45, tol)
+        try:
+            ens.ens_set_launch(ctx, launch)
+            ens.ens_solve(ctx)
+            assert ens.ens_sync(ctx) == ens.ENS_OK
+            ens.ens_solve(ctx)
+            assert ens.ens_sync(ctx) == ens.ENS_OK
+            trials = ens.ens_read(ctx, ens.ENS_NSTEPS) + ens.ens_read(ctx, ens.ENS_NREJ)
+            return ens.ens_kernel_ms(ctx), trials
+        finally:
+            ens.ens_destroy(ctx)
+
+    if case == "trial_distribution":
+        _, full = solve(C, km["y0"], 64, ens.make_launch(block=160, blocks_per_sm=1, cost_order=1))
+        _, pilot = solve(C, km["y0"], 1, ens.make_launch(block=160, blocks_per_sm=1, cost_order=0))
+        srt = np.sort(full)[::-1]
+        rank = lambda a: np.argsort(np.argsort(a))
+        print(json.dumps({"probe": case, "systems": int(full.size), "trials": int(full.sum()),
+                          "mean": float(full.mean()), "max": int(full.max()),
+                          "quantiles": {q: float(np.percentile(full, q)) for q in (50, 90, 99, 99.9)},
+                          "top_k_min_and_share": {k: [int(srt[k - 1]), float(srt[:k].sum() / full.sum())]
+                                                  for k in (10, 100, 1000, 10000)},
+                          "pilot_rank_correlation": float(np.corrcoef(rank(full), rank(pilot))[0, 1])}), flush=True)
+        return
+    if case != "pipe_sharing":
+        raise SystemExit(f"unknown probe {case}")
+    _, full = solve(C, km["y0"], 64, ens.make_launch(block=160, blocks_per_sm=1, cost_order=1))
+    i = int(np.argmax(full))            # the sweep's longest system
+    PL = ens.ENS_LAUNCH_PLAIN
+    rows = []
+    for label, n, block in (("1 warp, 1 lane", 1, 32), ("1 warp, 32 lanes", 32, 32), ("2 warps", 64, 64),
+                            ("4 warps, one per sub-partition", 128, 128), ("5 warps", 160, 160),
+                            ("8 warps, two per sub-partition", 256, 256), ("4 warps on every SM", 128 * 152, 128),
+                            ("5 warps on every SM", 160 * 152, 160)):
+        Cn = np.repeat(C[:, i:i + 1], n, axis=1)
+        y0 = np.repeat(km["y0"][:, i:i + 1], n, axis=1)
+        ms, tr = solve(Cn, y0, 16, ens.make_launch(mode=PL, block=block))
+        rows.append({"case": label, "systems": n, "block": block, "ms": ms, "trials": int(tr[0]),
+                     "us_per_trial": 1e3 * ms / float(tr[0])})
+    print(json.dumps({"probe": case, "system": i, "pA": float(ph["pA1"][i]), "f": float(ph["f1"][i]),
+                      "periods": 16, "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile", default=None,
-                    help="run one small case for ncu (km, km_full64, km_full2, km_fp32c, km_fp32x2, mlp_screen, "
+                    help="run one small case for ncu (km, km_full64, km_full2, km_pow, km_fp32c, km_fp32x2, mlp_screen, "
                          "mlp_screen_mma, mlp_train, prv, prv_df, x2p, lorenz)")
+    ap.add_argument("--probe", default=None, help="timing probe (pipe_sharing, trial_distribution)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -1126,6 +1218,9 @@ def main():
     args = ap.parse_args()
     if args.profile:
         run_profile_case(args.profile)
+        return
+    if args.probe:
+        run_probe(args.probe)
         return
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
