@@ -60,12 +60,12 @@ struct KmForcing {
   }
   __device__ __forceinline__ void eval(double tau, DF& fs, DF& fc) const {
     double s1, c1;
-    sincos2pi_poly(tau, &s1, &c1);
+    sincos2pi_poly<false>(tau, &s1, &c1);
     fs = df::mul(C5, df::from_double(s1));
     fc = df::mul(C7, df::from_double(c1));
     if (DUAL) {
       double s2, c2;
-      sincos2pi_poly(fma(C11, tau, C12f), &s2, &c2);
+      sincos2pi_poly<false>(fma(C11, tau, C12f), &s2, &c2);
       fs = df::add(df::mul(C6, df::from_double(s2)), fs);
       fc = df::add(df::mul(C8, df::from_double(c2)), fc);
     }

@@ -169,10 +169,22 @@ __device__ __forceinline__ int round4x(double x, double* kd) {
 // and absolute error of 1 + r^2 Q below 2e-17 after rounding the coefficients
 // to double (`gen_sincos2pi.py` next to this file recomputes them).  The
 // k mod 4 quarter turns then select and negate (the sign flips are integer
-// XORs on the high word).  16 FP64 instructions.
+// XORs on the high word).  16 FP64 instructions.  INT_ROUND = false takes k
+// from the 1.5 * 2^52 shift instead (18 FP64 instructions, fewer integer ones
+// and registers: the choice of the double-float kernels, whose FP32 and
+// integer pipes are the busy ones).
+template <bool INT_ROUND = true>
 __device__ __forceinline__ void sincos2pi_poly(double x, double* sn, double* cs) {
   double k;
-  const int q = round4x(x, &k);
+  int q;
+  if (INT_ROUND) {
+    q = round4x(x, &k);
+  } else {
+    const double shift = 6755399441055744.0;  // 1.5 * 2^52
+    const double t = fma(x, 4.0, shift);
+    q = __double2loint(t);
+    k = t - shift;
+  }
   const double r = fma(k, -0.25, x);
   const double u = r * r;
   double p = 0x1.e3eed5d16d705p+1;
