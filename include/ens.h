@@ -171,10 +171,17 @@ typedef struct {
  *                  the first call and replay it afterwards.
  *   cost_order     persistent mode: claim systems in decreasing order of their
  *                  step count in a one-phase pilot solve (longest first).
- *   systems_per_thread  RK4: 1, 2 or 4 systems integrated by each thread,
- *                  their steps interleaved in one instruction stream (0 means
- *                  1); each system's arithmetic is that of one per thread, so
- *                  results do not change.  The adaptive solvers take 1. */
+ *   systems_per_thread  systems integrated by each thread, their steps
+ *                  interleaved in one instruction stream (0 means 1); each
+ *                  system's arithmetic is that of one per thread, so results
+ *                  do not change.  RK4: 1, 2 or 4.  Adaptive: 1, or 2 for the
+ *                  FP64 Cash-Karp phase mode of the Keller-Miksis model with
+ *                  one driving frequency and C10 = 21/5, persistent mode, at
+ *                  most 128 threads per block (both slots of a lane claim
+ *                  systems; each iteration computes both slots' trials).
+ *                  Other combinations: ENS_ENOTSUP from ens_set_launch, or
+ *                  from ens_solve where the parameters decide (a second
+ *                  frequency or another exponent). */
 enum { ENS_LAUNCH_PLAIN = 0, ENS_LAUNCH_PERSISTENT = 1 };
 typedef struct {
     int32_t mode;
@@ -279,7 +286,8 @@ int32_t ens_npar(const ens_ctx *ctx);
  * kept) and writes it to *best (may be NULL).
  *   RK4: block 32..256 x systems_per_thread 1, 2, 4 on 1/8 of the steps.
  *   Adaptive: persistent launches of 3 to 24 warps per SM with longest-first
- *   claiming, the best residency without it, and a plain launch, each on
+ *   claiming, the best residency without it, a plain launch and, where the
+ *   kernel exists, two systems per thread at 6 and 8 warps per SM, each on
  *   1/8 of the phases (or of the time span) of every system -- the horizon is
  *   cut, not the ensemble, so the balance between throughput and the
  *   longest system's chain stays that of the full solve; the fraction is

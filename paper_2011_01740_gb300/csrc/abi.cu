@@ -19,6 +19,7 @@ cudaError_t launch_ck45(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch
 cudaError_t launch_ck45_fp32c(unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_ck45_df(unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_ck45_df_events(const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
+cudaError_t launch_ck45_spt2(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s);
 cudaError_t launch_order(const int64_t* steps, int64_t n, int32_t* order, unsigned* hist,
                          cudaStream_t s);
 cudaError_t launch_rhs_eval(int sys, unsigned flags, int64_t n, const double* P, const double* t,
@@ -184,8 +185,22 @@ cudaError_t launch_adaptive(const ens_ctx* c, const AdaptArgs& a, AdaptLaunch L,
   if (c->tol.prec == ENS_FP32_COMP) return launch_ck45_fp32c(c->km_flags, a, L, s);
   if (c->tol.prec == ENS_FP32X2)
     return c->sys == ENS_SYS_RELIEF_VALVE ? launch_ck45_df_events(a, L, s) : launch_ck45_df(c->km_flags, a, L, s);
+  if (L.spt == 2) return launch_ck45_spt2(c->sys, c->km_flags, a, L, s);
   return launch_ck45(c->sys, c->km_flags, a, L, s);
 }
+
+// Two systems per thread: the FP64 Cash-Karp phase mode of the Keller-Miksis
+// model with one driving frequency and the exponent 21/5, persistent launch
+// of at most 128 threads per block.  The static part is checked when the
+// launch is set, the parameter-dependent part (km_flags) when it runs.
+bool spt2_static_ok(const ens_ctx* c, const ens_launch& L) {
+  return c->solver == ENS_RKCK45 && c->sys == ENS_SYS_KELLER_MIKSIS && c->tol.n_phases > 0 &&
+         (c->tol.prec == ENS_FP64 || c->tol.prec == ENS_FP64_STRICT) && L.mode == ENS_LAUNCH_PERSISTENT &&
+         L.block <= 128;
+}
+const char* kSpt2Msg =
+    "systems_per_thread 2 runs the FP64 Cash-Karp phase mode of the Keller-Miksis model (one driving frequency, "
+    "C10 = 21/5) in a persistent launch of at most 128 threads per block; the other adaptive solves take 1";
 
 AdaptArgs adapt_args(ens_ctx* c) {
   AdaptArgs a{};
@@ -225,9 +240,11 @@ AdaptArgs adapt_args(ens_ctx* c) {
 AdaptLaunch adapt_launch(const ens_ctx* c, const ens_launch& L) {
   AdaptLaunch out;
   out.block = L.block;
+  out.spt = spt_of(L);
   if (L.mode == ENS_LAUNCH_PERSISTENT) {
     out.grid = (int64_t)c->sm_count * L.blocks_per_sm;
-    const int64_t need = (c->n + L.block - 1) / L.block;  // never more lanes than systems
+    const int64_t slots = (int64_t)L.block * out.spt;
+    const int64_t need = (c->n + slots - 1) / slots;  // never more lanes than systems
     if (out.grid > need) out.grid = need;
     if (out.grid < 1) out.grid = 1;
   } else {
@@ -302,8 +319,9 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, double
     set_err(c, "ENS_FP32X2 needs C10 = 21/5 (polytropic exponent 1.4) in every system");
     return ENS_ENOTSUP;
   }
-  if (spt_of(L) != 1) {
-    set_err(c, "the adaptive kernels run one system per thread (systems_per_thread 1)");
+  if (spt_of(L) != 1 &&
+      (spt_of(L) != 2 || !spt2_static_ok(c, L) || (c->km_flags & (kKmDual | kKmGeneralExponent)))) {
+    set_err(c, "%s", kSpt2Msg);
     return ENS_ENOTSUP;
   }
   AdaptArgs a = adapt_args(c);
@@ -568,8 +586,8 @@ ens_status ens_set_launch(ens_ctx* c, const ens_launch* cfg) {
     set_err(c, "RK4 runs a plain launch (systems_per_thread systems per thread)");
     return ENS_ENOTSUP;
   }
-  if (c->solver != ENS_RK4 && spt_of(L) != 1) {
-    set_err(c, "the adaptive solvers run one system per thread (systems_per_thread 1)");
+  if (c->solver != ENS_RK4 && spt_of(L) != 1 && (spt_of(L) != 2 || !spt2_static_ok(c, L))) {
+    set_err(c, "%s", kSpt2Msg);
     return ENS_ENOTSUP;
   }
   c->launch = L;
@@ -804,6 +822,13 @@ ens_status ens_autotune(ens_ctx* c, void* stream, ens_launch* best) {
         if (sh[0] == best_w) st = consider(mk(ENS_LAUNCH_PERSISTENT, sh[1], sh[2], 0, 1));
     }
     if (st == ENS_OK) st = consider(mk(ENS_LAUNCH_PLAIN, 128, 0, 0, 1));
+    // two systems per thread where the kernel exists: 6 and 8 warps per SM
+    // (236 registers a thread leave room for 8), longest first
+    for (const int b : {96, 128}) {
+      const ens_launch L2 = mk(ENS_LAUNCH_PERSISTENT, b, 2, 1, 2);
+      if (st == ENS_OK && spt2_static_ok(c, L2) && !(c->km_flags & (kKmDual | kKmGeneralExponent)))
+        st = consider(L2);
+    }
     c->order_ready = false;
   }
   if (st != ENS_OK) return st;

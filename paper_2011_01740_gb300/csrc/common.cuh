@@ -110,6 +110,7 @@ struct AdaptArgs {
 struct AdaptLaunch {
   int64_t grid;
   int block;
+  int spt = 1;  // systems per thread (2: the persistent Keller-Miksis phase-mode kernel)
 };
 
 // Nanosecond wall clock of the GPU (PTX %globaltimer).

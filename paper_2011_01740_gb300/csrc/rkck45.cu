@@ -335,6 +335,170 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Phase mode with two systems per thread (persistent launch, Cash-Karp): each
+// lane holds two slots, each claiming systems like a lane of
+// ck_phased_kernel.  Per iteration both slots' first stage and trial are
+// computed in one straight-line block, independent chains that the compiler
+// interleaves for the FP64 pipe; then each slot's accept / reject / phase-end
+// logic runs.  Persistent launches only: the slots claim from the counter.  The first stage is evaluated in every iteration, also after a
+// rejection, where its inputs are those of the last evaluation, so every
+// value equals that of one system per thread bit for bit (the right-hand-side
+// count counts only the evaluations that were needed).  A slot without work
+// computes on its last values and stores nothing.
+// ---------------------------------------------------------------------------
+template <class Sys>
+struct PhaseSlot {
+  Sys s;
+  typename Sys::Drive d0, dk, d5;  // drive at the phase start, at tau, at tau + h
+  double y[Sys::kDim], k1[Sys::kDim], y5[Sys::kDim], err[Sys::kDim];
+  double tau, dt, ymax, ymin, h, E, fac;
+  int64_t i;
+  int32_t ph, st;
+  uint32_t trials, nacc, nrej, nrhs;
+  bool k1v, clamped;
+};
+
+template <class Sys>
+__global__ void __launch_bounds__(128) ck_phased2_kernel(AdaptArgs a) {
+  static_assert(Sys::kPhaseRows == 0, "two systems per thread: systems without a phase hook");
+  constexpr int D = Sys::kDim;
+  constexpr int SPT = 2;
+  const double tau_end = a.t0 + a.phase_len;
+  const uint64_t deadline = global_ns() + a.timeout_ns;
+  bool timed_out = false;
+  uint32_t iter = 0;
+  PhaseSlot<Sys> S[SPT];
+
+  auto start_system = [&](PhaseSlot<Sys>& L) {
+    L.s.load(a.params, a.n, L.i);
+#pragma unroll
+    for (int c = 0; c < D; ++c) L.y[c] = a.y0[c * a.n + L.i];
+    L.tau = a.t0;
+    L.dt = a.dt0;
+    L.ph = 0;
+    L.st = timed_out ? kStTimeout : 0;
+    L.trials = L.nacc = L.nrej = L.nrhs = 0;
+    L.k1v = false;
+    L.ymax = L.ymin = L.y[0];
+    L.d0 = L.s.drive(a.t0);
+    L.dk = L.d0;
+  };
+  auto finish_system = [&](PhaseSlot<Sys>& L) {
+    const int64_t sys = L.i;
+    for (int p = max(L.ph, a.n_transient); p < a.n_phases; ++p) {
+      a.acc[(int64_t)(2 * (p - a.n_transient)) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
+      a.acc[(int64_t)(2 * (p - a.n_transient) + 1) * a.n + sys] = __longlong_as_double(0x7ff8000000000000LL);
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) a.y[c * a.n + sys] = L.y[c];
+    a.t_out[sys] = L.tau;
+    a.dt_out[sys] = L.dt;
+    a.status[sys] = L.st;
+    a.nacc[sys] = L.nacc;
+    a.nrej[sys] = L.nrej;
+    a.nrhs[sys] = L.nrhs;
+    if (L.st) atomicOr(&a.scratch->any_status, (unsigned)L.st);
+  };
+
+  // a slot without a first system computes on a copy of system 0 (n > 0)
+#pragma unroll
+  for (int q = 0; q < SPT; ++q) {
+    const int64_t k = claim(a, true);
+    S[q].i = k >= 0 ? k : 0;
+    start_system(S[q]);
+    S[q].i = k;
+  }
+  while (S[0].i >= 0 || S[1].i >= 0) {
+    if ((++iter & 127u) == 0 && global_ns() > deadline) timed_out = true;
+    // per slot: budgets and the step of this iteration
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+      PhaseSlot<Sys>& L = S[q];
+      if (L.i >= 0 && L.st == 0) {
+        if (timed_out) L.st |= kStTimeout;
+        else if (L.trials >= (uint64_t)a.max_steps) L.st |= kStMaxSteps;
+      }
+      L.h = L.dt;
+      L.clamped = false;
+      const double rest = tau_end - L.tau;
+      if (nnbits(L.h) >= nnbits(rest)) {
+        L.h = rest;
+        L.clamped = true;
+      }
+    }
+    // both slots' first stage and trial: independent straight-line chains
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+      PhaseSlot<Sys>& L = S[q];
+      L.s.fd(L.dk, L.tau, L.y, L.k1);
+      ck_trial(L.s, L.tau, L.h, L.y, L.k1, L.y5, L.err, L.d5);
+      L.E = err_norm<D>(L.y, L.y5, L.err, a.rtol, a.atol);
+      L.fac = step_factor(L.E);
+    }
+    // per slot: the outcome
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+      PhaseSlot<Sys>& L = S[q];
+      if (L.i < 0) continue;
+      bool sys_done = false;
+      if (L.st != 0) {
+        // close the current phase with what it has, then retire the system
+        if (L.ph < a.n_phases) {
+          if (L.ph >= a.n_transient) {
+            a.acc[(int64_t)(2 * (L.ph - a.n_transient)) * a.n + L.i] = L.ymax;
+            a.acc[(int64_t)(2 * (L.ph - a.n_transient) + 1) * a.n + L.i] = L.ymin;
+          }
+          ++L.ph;
+        }
+        sys_done = true;
+      } else {
+        if (!L.k1v) {
+          ++L.nrhs;
+          L.k1v = true;
+        }
+        L.nrhs += pair_rhs(kCashKarp);
+        ++L.trials;
+        if (accept(L.E)) {
+          L.tau = L.clamped ? tau_end : L.tau + L.h;
+          L.dk = L.d5;
+#pragma unroll
+          for (int c = 0; c < D; ++c) L.y[c] = L.y5[c];
+          L.k1v = false;
+          ++L.nacc;
+          L.ymax = omax(L.ymax, L.y[0]);
+          L.ymin = omin(L.ymin, L.y[0]);
+          if (!L.clamped) L.dt = bounded_step(L.h, L.fac, a.dt_min, a.dt_max);
+          if (okey(L.tau) >= okey(tau_end)) {
+            if (L.ph >= a.n_transient) {
+              a.acc[(int64_t)(2 * (L.ph - a.n_transient)) * a.n + L.i] = L.ymax;
+              a.acc[(int64_t)(2 * (L.ph - a.n_transient) + 1) * a.n + L.i] = L.ymin;
+            }
+            ++L.ph;
+            if (L.ph >= a.n_phases) {
+              sys_done = true;
+            } else {
+              L.tau = a.t0;
+              L.dk = L.d0;
+              L.k1v = false;
+              L.ymax = L.ymin = L.y[0];
+            }
+          }
+        } else {
+          ++L.nrej;
+          L.dt = L.h * L.fac;
+          if (nnbits(L.dt) < nnbits(a.dt_min)) L.st |= kStDtUnderflow;
+        }
+      }
+      if (sys_done) {
+        finish_system(L);
+        L.i = claim(a, false);
+        if (L.i >= 0) start_system(L);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Event mode (pressure relief valve, Sec. 4.3).  Events g1 = y1 (impact,
 // body reaching the seat while moving towards it) and g2 = y2 (local maximum
 // of y1, the Poincare section), both falling, absolute tolerance event_tol:
@@ -664,6 +828,18 @@ cudaError_t launch_pair(int sys, unsigned flags, const AdaptArgs& a, dim3 g, dim
       default: return cudaErrorInvalidValue;
     }
   }
+  return cudaGetLastError();
+}
+
+// Two systems per thread: the Keller-Miksis phase mode with Cash-Karp, one
+// driving frequency and the exponent 21/5, persistent lanes.
+cudaError_t launch_ck45_spt2(int sys, unsigned flags, const AdaptArgs& a, AdaptLaunch L, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  if (sys != ENS_SYS_KELLER_MIKSIS || a.n_phases <= 0 || a.pair != kCashKarp || !a.persistent ||
+      (flags & (kKmDual | kKmGeneralExponent)))
+    return cudaErrorNotSupported;
+  if (L.grid <= 0 || L.grid > 0x7fffffffLL || L.block <= 0 || L.block > 128) return cudaErrorInvalidConfiguration;
+  ck_phased2_kernel<KellerMiksis<false, true>><<<dim3((unsigned)L.grid), dim3((unsigned)L.block), 0, s>>>(a);
   return cudaGetLastError();
 }
 

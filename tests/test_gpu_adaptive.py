@@ -329,10 +329,11 @@ def test_kernel_ms_times_the_main_launch(use_graph):
 
 def test_autotune_of_the_adaptive_solve():
     """The tuner times persistent launches of 3-24 warps per SM with
-    longest-first claiming, the best residency without it and a plain launch,
-    on a shortened horizon of every system (1/8 of 16 phases), keeps the
-    fastest, and leaves results unchanged: the claim order and the launch
-    shape never change what a system computes."""
+    longest-first claiming, the best residency without it, a plain launch and
+    two systems per thread at 6 and 8 warps per SM, on a shortened horizon of
+    every system (1/8 of 16 phases), keeps the fastest, and leaves results
+    unchanged: the claim order and the launch shape never change what a
+    system computes."""
     km = W.km(24, 20, n_phases=16)
     C = km_coeffs_lib(km["phys"], km["liquid"])
     ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
@@ -343,16 +344,18 @@ def test_autotune_of_the_adaptive_solve():
         ref = {w: ens.ens_read(ctx, w) for w in (ens.ENS_ACC, ens.ENS_STATE, ens.ENS_NSTEPS)}
         best = ens.ens_autotune(ctx)
         rows = ens.ens_autotune_table(ctx)
-        assert len(rows) == 11
+        assert len(rows) == 13
         assert all(r["horizon_frac"] == 0.125 for r in rows)
         persistent = [r for r in rows if r["launch"]["mode"] == ens.ENS_LAUNCH_PERSISTENT]
-        warps = {r["launch"]["block"] // 32 * r["launch"]["blocks_per_sm"] for r in persistent}
-        assert warps == {3, 4, 5, 6, 7, 8, 12, 16, 24}
+        warps = lambda rs: {r["launch"]["block"] // 32 * r["launch"]["blocks_per_sm"] for r in rs}
+        assert warps(r for r in persistent if r["launch"]["systems_per_thread"] == 1) == {3, 4, 5, 6, 7, 8, 12, 16, 24}
+        assert warps(r for r in persistent if r["launch"]["systems_per_thread"] == 2) == {6, 8}
         assert any(r["launch"]["mode"] == ens.ENS_LAUNCH_PLAIN for r in rows)
         assert any(r["launch"]["cost_order"] == 0 for r in persistent)
         fastest = min(rows, key=lambda r: r["ms"])["launch"]
-        assert (fastest["mode"], fastest["block"], fastest["blocks_per_sm"], fastest["cost_order"]) == \
-            (best.mode, best.block, best.blocks_per_sm, best.cost_order)
+        assert (fastest["mode"], fastest["block"], fastest["blocks_per_sm"], fastest["cost_order"],
+                fastest["systems_per_thread"]) == \
+            (best.mode, best.block, best.blocks_per_sm, best.cost_order, max(1, best.systems_per_thread))
         ens.ens_solve(ctx)
         assert ens.ens_sync(ctx) == ens.ENS_OK
         for w, v in ref.items():
@@ -365,61 +368,76 @@ def test_autotune_of_the_adaptive_solve():
         ens.ens_destroy(ctx)
 
 
-def test_adaptive_solvers_refuse_several_systems_per_thread():
+_ALL_OUT = ("y", "acc", "status", "nacc", "nrej", "nrhs", "t", "dt")
+
+
+@pytest.mark.parametrize("block,bps,cost_order,m,tolkw", [
+    (128, 2, 1, (19, 23), {}),                          # 437 systems, ragged against 2 x 128 slots a lane pair
+    (96, 2, 0, (19, 23), {"n_transient": 2}),           # transient phases, counter order
+    (64, 1, 1, (1, 5), {}),                             # 5 systems: most slots never get one
+    (128, 2, 1, (19, 23), {"max_steps": 150}),          # budget runs out mid-phase: NaN rows, status
+])
+def test_two_systems_per_thread_give_the_same_bits(block, bps, cost_order, m, tolkw):
+    """Two systems per thread in the persistent phase-mode kernel: every output
+    equals that of one system per thread bit for bit (each slot's step
+    sequence is that of a lane of its own), with ragged ends, slots that never
+    claim a system, transient phases and systems retired by the step budget."""
+    km = W.km(*m, n_phases=6)
+    one = _km_gpu(km, launch=ens.make_launch(block=128, blocks_per_sm=2, cost_order=cost_order), **tolkw)
+    two = _km_gpu(km, launch=ens.make_launch(block=block, blocks_per_sm=bps, cost_order=cost_order,
+                                             systems_per_thread=2), **tolkw)
+    assert two["launch"]["systems_per_thread"] == 2
+    assert one["sync"] == two["sync"]
+    if "max_steps" in tolkw:
+        assert np.any(one["status"] != 0) and np.any(np.isnan(one["acc"]))
+    else:
+        assert one["sync"] == ens.ENS_OK and np.all(one["status"] == 0)
+    for k in _ALL_OUT:
+        assert np.array_equal(one[k], two[k], equal_nan=True), k
+
+
+def test_systems_per_thread_outside_the_kernel_that_has_it_are_refused():
+    """Two systems per thread exist for the FP64 Cash-Karp phase mode of the
+    Keller-Miksis model with one frequency and exponent 21/5, persistent, at
+    most 128 threads a block; everything else is refused with ENS_ENOTSUP:
+    when the launch is set, or, for a second driving frequency (a parameter
+    property), when the solve is enqueued."""
     km = W.km(4, 4, n_phases=2)
     C = km_coeffs_lib(km["phys"], km["liquid"])
-    ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
-                         ens.ENS_RKCK45, ens_tol_from(km["tol"]))
-    try:
+    tol = ens_tol_from(km["tol"])
+
+    def refused(ctx, **kw):
         with pytest.raises(ens.EnsError) as e:
-            ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1, systems_per_thread=2))
+            ens.ens_set_launch(ctx, ens.make_launch(**kw))
         assert e.value.status == ens.ENS_ENOTSUP
         assert ens.ens_get_launch(ctx).systems_per_thread in (0, 1)
+
+    ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0), ens.ENS_RKCK45, tol)
+    try:
+        refused(ctx, block=128, blocks_per_sm=1, systems_per_thread=4)
+        refused(ctx, block=256, blocks_per_sm=1, systems_per_thread=2)
+        refused(ctx, mode=ens.ENS_LAUNCH_PLAIN, block=128, systems_per_thread=2)
+        ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1, systems_per_thread=2))
+        assert ens.ens_get_launch(ctx).systems_per_thread == 2
     finally:
         ens.ens_destroy(ctx)
-
-
-# ---------------------------------------------------------------------------
-# split-precision (FP32 + compensated) Keller-Miksis variant
-# ---------------------------------------------------------------------------
-
-def test_km_fp32_compensated_error_against_fp64_oracle():
-    """FP32 right-hand side and compensated stage sums, float-pair state, FP64
-    time and acceptance.  Per-period maxima are sampled at step points, so any
-    run at another tolerance differs from the tol 1e-10 oracle by the
-    sampling error of its step sequence; the FP32 variant is therefore
-    compared with the FP64 kernel at the same tolerance: split precision must
-    not add error beyond what that tolerance costs in FP64."""
-    km = W.km(19, 23, n_phases=4)
-    Co = km_coeffs_oracle(km["phys"], km["liquid"])
-    r, well = _well_conditioned(oracle.KM, Co, km["y0"], oracle_tol_from(km["tol"]))
-    report = {}
-    for tol in (1e-7, 1e-8):
-        g32 = _km_gpu(km, prec=ens.ENS_FP32_COMP, rtol=tol, atol=tol)
-        g64 = _km_gpu(km, rtol=tol, atol=tol)
-        assert g32["sync"] == ens.ENS_OK and np.all(g32["status"] == 0)
-        assert np.all(np.isfinite(g32["acc"]))
-        e32 = rel_err(g32["acc"], r["acc"])[well]
-        e64 = rel_err(g64["acc"], r["acc"])[well]
-        report[tol] = (np.median(e32), np.median(e64), np.percentile(e32, 90), np.percentile(e64, 90),
-                       g32["nacc"].sum() / g64["nacc"].sum())
-        print(f"tol {tol:g}: fp32c median {report[tol][0]:.2e} p90 {report[tol][2]:.2e} | "
-              f"fp64 median {report[tol][1]:.2e} p90 {report[tol][3]:.2e} | steps ratio {report[tol][4]:.3f}")
-        assert np.median(e32) < 3 * np.median(e64) + 1e-6
-        assert np.percentile(e32, 90) < 3 * np.percentile(e64, 90) + 1e-5
-
-
-def test_km_fp32_compensated_launch_shapes_are_bitwise_identical():
-    """The split-precision kernel gives the same bits under every launch shape,
-    including the high-occupancy persistent shapes (24 warps/SM) that the
-    1024 x 1024 benchmark run uses."""
-    km = W.km(40, 50, n_phases=3)          # 2,000 systems
-    kw = dict(prec=ens.ENS_FP32_COMP, rtol=1e-8, atol=1e-8)
-    ref = _km_gpu(km, launch=ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=128), **kw)
-    assert ref["sync"] == ens.ENS_OK and np.all(ref["status"] == 0)
-    for L in (ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=256, blocks_per_sm=3, cost_order=1),
-              ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=128, blocks_per_sm=6, use_graph=1),
-              ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=32, blocks_per_sm=1)):
-        g = _km_gpu(km, launch=L, **kw)
-        for k in ("y", "acc", "nacc", "nrej", "nrhs", "status", "dt"):
-            assert np.array_equal(g[k], ref[k], equal_nan=True), (k, L.as_dict())
+    for solver, prec in ((ens.ENS_DOPRI5, ens.ENS_FP64), (ens.ENS_RKCK45, ens.ENS_FP32X2)):
+        ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0), solver,
+                             ens_tol_from(km["tol"], prec=prec))
+        try:
+            refused(ctx, block=128, blocks_per_sm=1, systems_per_thread=2)
+        finally:
+            ens.ens_destroy(ctx)
+    # a second driving frequency: accepted as a launch, refused by the solve
+    phys = dict(km["phys"])
+    phys["pA2"] = np.full(16, 2.0e4)
+    phys["f2"] = np.full(16, 5.0e4)
+    C2 = km_coeffs_lib(phys, km["liquid"])
+    ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C2.shape[1], C2, km["y0"], (0.0, 1.0), ens.ENS_RKCK45, tol)
+    try:
+        ens.ens_set_launch(ctx, ens.make_launch(block=128, blocks_per_sm=1, systems_per_thread=2))
+        with pytest.raises(ens.EnsError) as e:
+            ens.ens_solve(ctx)
+        assert e.value.status == ens.ENS_ENOTSUP
+    finally:
+        ens.ens_destroy(ctx)
