@@ -34,14 +34,18 @@ from paper_2011_01740_gb300 import workloads as W  # noqa: E402
 # the Keller-Miksis kernel, and per RK4 step of the x' = x^2 - p and Lorenz
 # kernels, from the ncu instruction counters of profiles/ (None until
 # measured: the roofline then reports achieved = null).
-FLOPS_PER_KM_TRIAL = 589.91  # 232.61 DFMA + 121.70 DMUL + 2.98 DADD per trial (profiles/)
-# all FP64 thread instructions per trial (DFMA, DMUL, DADD, compares, min/max),
-# for the FP64 pipe's instruction-issue fraction
-FP64_INST_PER_KM_TRIAL = 357.29
+FLOPS_PER_KM_TRIAL = 439.90  # 162.61 DFMA + 111.70 DMUL + 2.98 DADD per trial (profiles/)
+# all FP64 thread instructions per trial, for the FP64 pipe's issue fraction
+FP64_INST_PER_KM_TRIAL = 277.29
+# The same trial with the forcing's sine and cosine as FP64 polynomials (the
+# earlier kernel: 232.61 DFMA + 121.70 DMUL + 2.98 DADD, profiles/); the
+# integer-pipe sine and cosine take 150 of these flops off the FP64 pipe.
+# Reported beside the executed count as the trial's FP64-equivalent work.
+FLOPS_FP64_FORM_KM_TRIAL = 589.91
 # DRAM bytes (read + write) of one benchmarked Keller-Miksis launch, from the
 # one-pass ncu capture in profiles/ (inputs 15.7 MB read once, 134 MB of
 # per-period accessories written once); None once the kernel changes.
-KM_LAUNCH_DRAM_BYTES = 33905152 + 116558592
+KM_LAUNCH_DRAM_BYTES = 33731072 + 114730496
 FLOPS_PER_X2P_STEP = 21.0     # 10 DFMA + 1 DADD (Sec. 3.2.2 counters; kernel counted by ncu)
 FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast kernel
 # executed flops per trial of the other adaptive kernels (ncu counts,
@@ -339,6 +343,9 @@ def km_roofline(trials: float, kernel_ms: float, accepted: float) -> dict:
             "fp64_inst_per_trial": FP64_INST_PER_KM_TRIAL,
             "fp64_issue_frac": (FP64_INST_PER_KM_TRIAL * trials / (kernel_ms / 1e3) / FP64_INST_PEAK
                                 if FP64_INST_PER_KM_TRIAL else None),
+            # the trial's flops in its all-FP64 form over the same time: what an
+            # FP64-only kernel would have to reach to match this one
+            "fp64_form_frac": FLOPS_FP64_FORM_KM_TRIAL * trials / (kernel_ms / 1e3) / FP64_PEAK,
             # the share of the work spent on accepted steps (rejected trials are discarded)
             "useful_frac": accepted / trials if trials else None}
 

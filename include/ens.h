@@ -284,7 +284,9 @@ int32_t ens_npar(const ens_ctx *ctx);
  * and Sec. 4.1.2).  Times candidate launches on this context with shortened
  * solves on `stream`, keeps the fastest as the context's launch (use_graph is
  * kept) and writes it to *best (may be NULL).
- *   RK4: block 32..256 x systems_per_thread 1, 2, 4 on 1/8 of the steps.
+ *   RK4: block 32..256 x systems_per_thread 1, 2, 4, each timed twice (the
+ *   faster time counts and is the one in the table), on the whole solve up
+ *   to 1e9 system-steps, else on 1/8 of the steps.
  *   Adaptive: persistent launches of 3 to 24 warps per SM with longest-first
  *   claiming, the best residency without it, a plain launch and, where the
  *   kernel exists, two systems per thread at 6 and 8 warps per SM, each on

@@ -771,7 +771,9 @@ ens_status ens_autotune(ens_ctx* c, void* stream, ens_launch* best) {
         st = time_one(L, &ms0);
         if (st == ENS_OK) st = time_one(L, &ms1);
         if (st != ENS_OK) break;
-        c->tune_rows.erase(c->tune_rows.end() - 2);  // keep the second timing
+        // one row per candidate, holding the timing the choice uses (the faster)
+        c->tune_rows.erase(c->tune_rows.end() - 2);
+        c->tune_rows.back().ms = (double)std::min(ms0, ms1);
         if (std::min(ms0, ms1) < best_ms) {
           best_ms = std::min(ms0, ms1);
           best_L = L;

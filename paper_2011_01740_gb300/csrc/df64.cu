@@ -45,7 +45,11 @@ constexpr DF kSafety = pair_of(0.9);
 
 // forcing of the dual-frequency Keller-Miksis (KellerMiksis::drive): sin and
 // cos of the phase angles in FP64 (sincos2pi_poly), split into pairs, the
-// amplitude products and the sum of the two components in double-word
+// amplitude products and the sum of the two components in double-word.  The
+// FP64 polynomial, not the integer-pipe sincos2pi_fx of the FP64 kernels:
+// here the FP32 and integer pipes carry the step and the FP64 pipe is the
+// spare one (1024 x 1024 grid, 8 periods: 1.30 s against 1.64 s with
+// sincos2pi_fx).
 template <bool DUAL>
 struct KmForcing {
   DF C5, C6, C7, C8;
@@ -60,12 +64,12 @@ struct KmForcing {
   }
   __device__ __forceinline__ void eval(double tau, DF& fs, DF& fc) const {
     double s1, c1;
-    sincos2pi_poly<false>(tau, &s1, &c1);
+    sincos2pi_poly(tau, &s1, &c1);
     fs = df::mul(C5, df::from_double(s1));
     fc = df::mul(C7, df::from_double(c1));
     if (DUAL) {
       double s2, c2;
-      sincos2pi_poly<false>(fma(C11, tau, C12f), &s2, &c2);
+      sincos2pi_poly(fma(C11, tau, C12f), &s2, &c2);
       fs = df::add(df::mul(C6, df::from_double(s2)), fs);
       fc = df::add(df::mul(C8, df::from_double(c2)), fc);
     }

@@ -10,6 +10,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "sincos_fx.cuh"
 
 namespace ens {
 
@@ -131,60 +132,23 @@ __device__ __forceinline__ double sqrt_nr(double x) {
   return x * rr;
 }
 
-// A nearest integer k to 4x, and the double k, on the integer pipe from the
-// high word of x (the usual 1.5 * 2^52 shift would cost the FP64 pipe an FMA
-// and an addition).  With the high word's 21-bit significand m (implicit bit
-// included) and exponent field e, 4|x| = m 2^-(1041 - e) up to the low word;
-// for |x| < 2^18 the shift s = 1041 - e is at least 2 and k = (m + 2^(s-1))
-// >> s.  The low word can only matter when 4|x| lies within 2^-19 of a half,
-// where either neighbour leaves |x - k/4| <= 1/8 + 2^-21, inside the accuracy
-// of the polynomials below.  Larger |x| takes the FP64 shift instead.
-__device__ __forceinline__ int round4x(double x, double* kd) {
-  const int hi = __double2hiint(x);
-  const int e = (hi >> 20) & 0x7ff;
-  if (e >= 1023 + 18) {  // |x| >= 2^18 (and inf, NaN)
-    const double shift = 6755399441055744.0;  // 1.5 * 2^52
-    const double t = fma(x, 4.0, shift);
-    *kd = t - shift;
-    return __double2loint(t);
-  }
-  const unsigned m = ((unsigned)hi & 0xfffffu) | 0x100000u;
-  const int sh = 1041 - e;
-  unsigned k = sh > 31 ? 0u : ((m + (1u << (sh - 1))) >> sh);
-  unsigned kh = 0u;
-  if (k != 0u) {
-    const int lz = __clz(k);
-    kh = ((unsigned)(1054 - lz) << 20) | ((k << lz << 1) >> 12);
-  }
-  if (hi < 0) kh |= 0x80000000u;
-  *kd = __hiloint2double((int)kh, 0);
-  return hi < 0 ? -(int)k : (int)k;
-}
-
-// sin(2 pi x) and cos(2 pi x) together for |x| < 2^49.  The argument is split
-// exactly as x = k/4 + r with k a nearest integer to 4x (round4x, integer
-// pipe) and |r| <= 1/8 (x - k/4 is exact); sin(2 pi r) = r P(r^2) and
-// cos(2 pi r) = 1 + r^2 Q(r^2) with P, Q of degree 6 from a weighted minimax
-// fit (Remez exchange) on r^2 in [0, 1/64]: relative error of P below 5e-17
-// and absolute error of 1 + r^2 Q below 2e-17 after rounding the coefficients
-// to double (`gen_sincos2pi.py` next to this file recomputes them).  The
-// k mod 4 quarter turns then select and negate (the sign flips are integer
-// XORs on the high word).  16 FP64 instructions.  INT_ROUND = false takes k
-// from the 1.5 * 2^52 shift instead (18 FP64 instructions, fewer integer ones
-// and registers: the choice of the double-float kernels, whose FP32 and
-// integer pipes are the busy ones).
-template <bool INT_ROUND = true>
+// sin(2 pi x) and cos(2 pi x) together for |x| < 2^49, in FP64 arithmetic.
+// The argument is split exactly as x = k/4 + r with k the nearest integer to
+// 4x (the 1.5 * 2^52 shift) and |r| <= 1/8 (x - k/4 is exact);
+// sin(2 pi r) = r P(r^2) and cos(2 pi r) = 1 + r^2 Q(r^2) with P, Q of degree
+// 6 from a weighted minimax fit (Remez exchange) on r^2 in [0, 1/64]:
+// relative error of P below 5e-17 and absolute error of 1 + r^2 Q below 2e-17
+// after rounding the coefficients to double (`gen_sincos2pi.py` next to this
+// file recomputes them).  The k mod 4 quarter turns then select and negate
+// (the sign flips are integer XORs on the high word).  18 FP64 instructions.
+// The double-float kernels use it: their FP32 and integer pipes carry the
+// step, so the FP64 pipe is their spare one.  The FP64 kernels take the
+// integer-pipe sincos2pi_fx (sincos_fx.cuh) instead.
 __device__ __forceinline__ void sincos2pi_poly(double x, double* sn, double* cs) {
-  double k;
-  int q;
-  if (INT_ROUND) {
-    q = round4x(x, &k);
-  } else {
-    const double shift = 6755399441055744.0;  // 1.5 * 2^52
-    const double t = fma(x, 4.0, shift);
-    q = __double2loint(t);
-    k = t - shift;
-  }
+  const double shift = 6755399441055744.0;  // 1.5 * 2^52
+  const double t = fma(x, 4.0, shift);
+  const int q = __double2loint(t);
+  const double k = t - shift;
   const double r = fma(k, -0.25, x);
   const double u = r * r;
   double p = 0x1.e3eed5d16d705p+1;
@@ -229,9 +193,9 @@ struct NoDrive {};
 //   D_KM = y1 - C9 y1 y2 + C4 C9.
 // Following the paper's cost notes (Sec. 3.3): one reciprocal yields both
 // 1/y1 (shared by the three 1/y1 terms) and 1/D_KM, sine and cosine of one
-// angle come from one evaluation (sincos2pi_poly), and the rational power is
-// not sent through pow(): with EXP215 the exponent C10 = 3 gamma = 4.2 = 21/5
-// (gamma = 1.4) is applied as
+// angle come from one evaluation (sincos2pi_fx, on the integer pipe), and the
+// rational power is not sent through pow(): with EXP215 the exponent
+// C10 = 3 gamma = 4.2 = 21/5 (gamma = 1.4) is applied as
 //   (1/y1)^(21/5) = (1/y1)^4 * y1^(-1/5)
 // with y1^(-1/5) from inv_fifth_root (the host selects this form when every
 // system's C10 lies within 4 ulp of 21/5; otherwise pow() is used).
@@ -266,11 +230,11 @@ struct KellerMiksis {
   }
   __device__ __forceinline__ Drive drive(double tau) const {
     double s1, c1;
-    sincos2pi_poly(tau, &s1, &c1);
+    sincos2pi_fx(tau, &s1, &c1);
     Drive d{C5 * s1, C7 * c1};
     if (DUAL) {
       double s2, c2;
-      sincos2pi_poly(fma(C11, tau, C12f), &s2, &c2);
+      sincos2pi_fx(fma(C11, tau, C12f), &s2, &c2);
       d.fs = fma(C6, s2, d.fs);
       d.fc = fma(C8, c2, d.fc);
     }
