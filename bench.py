@@ -34,23 +34,24 @@ from paper_2011_01740_gb300 import workloads as W  # noqa: E402
 # the Keller-Miksis kernel, and per RK4 step of the x' = x^2 - p and Lorenz
 # kernels, from the ncu instruction counters of profiles/ (None until
 # measured: the roofline then reports achieved = null).
-FLOPS_PER_KM_TRIAL = 439.90  # 162.61 DFMA + 111.70 DMUL + 2.98 DADD per trial (profiles/)
+FLOPS_PER_KM_TRIAL = 340.19  # 135.68 DFMA + 65.86 DMUL + 2.98 DADD per trial (profiles/)
 # all FP64 thread instructions per trial, for the FP64 pipe's issue fraction
-FP64_INST_PER_KM_TRIAL = 277.29
-# The same trial with the forcing's sine and cosine as FP64 polynomials (the
-# earlier kernel: 232.61 DFMA + 121.70 DMUL + 2.98 DADD, profiles/); the
-# integer-pipe sine and cosine take 150 of these flops off the FP64 pipe.
-# Reported beside the executed count as the trial's FP64-equivalent work.
+FP64_INST_PER_KM_TRIAL = 204.52
+# The same trial in its all-FP64 form (the forcing's sine and cosine, the
+# fifth root, the polytropic power and the error norm's reciprocals as FP64
+# arithmetic: 232.61 DFMA + 121.70 DMUL + 2.98 DADD, profiles/); the
+# fixed-point evaluations on the integer pipe take 250 of these flops off the
+# FP64 pipe.  Reported beside the executed count as the trial's FP64-form work.
 FLOPS_FP64_FORM_KM_TRIAL = 589.91
 # DRAM bytes (read + write) of one benchmarked Keller-Miksis launch, from the
 # one-pass ncu capture in profiles/ (inputs 15.7 MB read once, 134 MB of
 # per-period accessories written once); None once the kernel changes.
-KM_LAUNCH_DRAM_BYTES = 33731072 + 114730496
+KM_LAUNCH_DRAM_BYTES = 37872128 + 117764864
 FLOPS_PER_X2P_STEP = 21.0     # 10 DFMA + 1 DADD (Sec. 3.2.2 counters; kernel counted by ncu)
 FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast kernel
 # executed flops per trial of the other adaptive kernels (ncu counts,
 # profiles/; None until measured: their fractions are then null)
-FLOPS_PER_VALVE_TRIAL = 301.59        # FP64: 115.0 DFMA + 57.5 DMUL + 14.1 DADD, ck_events_kernel
+FLOPS_PER_VALVE_TRIAL = 273.36        # FP64: 102.92 DFMA + 53.42 DMUL + 14.10 DADD, ck_events_kernel
 FLOPS_FP32_PER_FP32C_TRIAL = 1516.0   # FP32: 441.1 FFMA + 162.4 FMUL + 471.4 FADD, ck_phased_fp32c_kernel
 FLOPS_FP32_PER_DF_TRIAL = 5277.6      # FP32: 746.1 FFMA + 454.9 FMUL + 3330.5 FADD, ck_phased_df_kernel
 FLOPS_FP32_PER_DF_VALVE_TRIAL = 3173.5  # FP32, ck_events_df_kernel

@@ -48,9 +48,16 @@ __device__ __forceinline__ Dual rcp_nr(Dual x) {
   return {r, -(r * r) * x.d};
 }
 // (x^(-1/5))' = -(1/5) x^(-1/5) x' / x
-__device__ __forceinline__ Dual inv_fifth_root(Dual x) {
-  const double r = inv_fifth_root(x.v);
+__device__ __forceinline__ Dual inv_fifth_root_fx(Dual x) {
+  const double r = inv_fifth_root_fx(x.v);
   return {r, -0.2 * r * x.d / x.v};
+}
+// g = y1^(-21/5): the value from the same fixed-point evaluation as the
+// plain right-hand side (so the tangent system's state part stays bitwise
+// that of KellerMiksis), g' = -(21/5) g y1' / y1 with rx = 1/y1
+__device__ __forceinline__ Dual polytropic_215(Dual y1, Dual rx) {
+  const double g = pow_m21_5_fx(y1.v);
+  return {g, (-4.2 * g) * (rx.v * y1.d)};
 }
 // (x^p)' = p x^p x' / x
 __device__ __forceinline__ Dual pow(Dual x, double p) {

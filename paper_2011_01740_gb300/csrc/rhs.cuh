@@ -10,6 +10,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "fifth_root_fx.cuh"
 #include "sincos_fx.cuh"
 
 namespace ens {
@@ -88,7 +89,10 @@ __device__ __forceinline__ double f32_to_f64(float v) {
 //   v <- v (1 + r / 5 + 3 r^2 / 25).
 // The neglected r^3 term (11 r^3 / 125) is below 2^-58 for the seed's
 // accuracy, so the result is within about 2 ulp of x^(-1/5).  Cost: 7 FP64
-// instructions, against roughly a hundred for pow().
+// instructions, against roughly a hundred for pow().  The FP64 kernels take
+// inv_fifth_root_fx (fifth_root_fx.cuh: the same step in fixed point on the
+// integer pipe); this one serves the double-float kernels' controller, whose
+// FP64 pipe is their spare one.
 __device__ __forceinline__ double inv_fifth_root(double x) {
   const float xf = f64_to_f32_trunc(x);
   float l, vf;
@@ -106,7 +110,12 @@ __device__ __forceinline__ double inv_fifth_root(double x) {
 // Newton-Raphson step, v (1 + e + e^2) with e = 1 - d v, which cubes the
 // seed's relative error.  Not correctly rounded; 3 FP64 instructions after
 // the seed.  Zero, infinite and subnormal d give NaN or garbage: callers use it
-// on values bounded away from those.
+// on values bounded away from those.  The right-hand side keeps this FP64 form
+// although rcp_fx (rcp_fx.cuh) moves the step to the integer pipe: the
+// reciprocal sits on the chain of every stage, and there the fixed-point
+// step's latency cost the tail-bound 362 x 362 sweep 6 % (2.48 s against
+// 2.34 s) for 4 % on the throughput-bound 1024 x 1024 grid.  The error norm,
+// off that chain, takes rcp_fx.
 __device__ __forceinline__ double rcp_nr(double d) {
   double v;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(v) : "d"(d));
@@ -175,6 +184,15 @@ __device__ __forceinline__ void sincos2pi_poly(double x, double* sn, double* cs)
   *cs = __hiloint2double((int)((unsigned)__double2hiint(b) ^ fb), __double2loint(b));
 }
 
+// (1/y1)^(21/5) for the Keller-Miksis polytropic term with gamma = 7/5: in
+// fixed point on the integer pipe from y1 alone (fifth_root_fx.cuh).  rx =
+// 1/y1 is not needed here; the tangent system's dual-number overload
+// (dual.cuh) takes its derivative from it.
+__device__ __forceinline__ double polytropic_215(double y1, double rx) {
+  (void)rx;
+  return pow_m21_5_fx(y1);
+}
+
 // Right-hand sides used by the adaptive kernels expose their time-only part
 // separately: drive(t) evaluates it, fd(d, t, y, dy) the rest.  A Cash-Karp
 // trial ends at t + h, where the next trial's first stage starts, so the
@@ -191,14 +209,14 @@ struct NoDrive {};
 //          - (C5 sin 2 pi tau + C6 sin(2 pi C11 tau + C12)) (1 + C9 y2)
 //          - y1 (C7 cos 2 pi tau + C8 cos(2 pi C11 tau + C12)),
 //   D_KM = y1 - C9 y1 y2 + C4 C9.
-// Following the paper's cost notes (Sec. 3.3): one reciprocal yields both
-// 1/y1 (shared by the three 1/y1 terms) and 1/D_KM, sine and cosine of one
-// angle come from one evaluation (sincos2pi_fx, on the integer pipe), and the
-// rational power is not sent through pow(): with EXP215 the exponent
-// C10 = 3 gamma = 4.2 = 21/5 (gamma = 1.4) is applied as
-//   (1/y1)^(21/5) = (1/y1)^4 * y1^(-1/5)
-// with y1^(-1/5) from inv_fifth_root (the host selects this form when every
-// system's C10 lies within 4 ulp of 21/5; otherwise pow() is used).
+// Following the paper's cost notes (Sec. 3.3): one reciprocal (rcp_nr)
+// yields both 1/y1 (shared by the three 1/y1 terms) and 1/D_KM, sine and
+// cosine of one angle come from one evaluation
+// (sincos2pi_fx, on the integer pipe), and the rational power is not sent
+// through pow(): with EXP215 the exponent C10 = 3 gamma = 4.2 = 21/5
+// (gamma = 1.4) is applied as y1^(-21/5) = (y1^(-1/5))^21 in fixed point
+// (polytropic_215; the host selects this form when every system's C10 lies
+// within 4 ulp of 21/5; otherwise pow() is used).
 // The two forcing sums depend on tau alone and form the Drive.
 // DUAL selects the second driving frequency (C6, C8 != 0).
 // ---------------------------------------------------------------------------
@@ -251,8 +269,7 @@ struct KellerMiksis {
     const T rx = D * w;
     T g;
     if (EXP215) {
-      const T rx2 = rx * rx;
-      g = (rx2 * rx2) * inv_fifth_root(y1);
+      g = polytropic_215(y1, rx);
     } else {
       g = pow(rx, C10);
     }

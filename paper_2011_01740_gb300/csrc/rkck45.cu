@@ -28,6 +28,7 @@
 #include "dual.cuh"
 #include "events.cuh"
 #include "fcmp.cuh"
+#include "rcp_fx.cuh"
 #include "rhs.cuh"
 
 namespace ens {
@@ -147,9 +148,9 @@ __device__ __forceinline__ void pair_trial(const Sys& s, double t, double h, con
 constexpr uint32_t pair_rhs(int PAIR) { return PAIR == kDormandPrince ? 6u : 5u; }
 
 // E = max_c |err_c| / (atol + rtol max(|y_c|, |y5_c|)), >= 0, or NaN (sign
-// clear) when a trial blew up.  rcp_nr is within 1 ulp of 1/sc for the
-// normal, finite sc of a solve; a zero, subnormal, infinite or NaN sc gives
-// NaN, and a NaN stays the maximum.
+// clear) when a trial blew up.  rcp_fx (integer pipe) is within half an ulp
+// plus 2^-57 of 1/sc for the normal sc below 2^1022 of a solve; a zero,
+// subnormal, infinite or NaN sc gives NaN, and a NaN stays the maximum.
 template <int D>
 __device__ __forceinline__ double err_norm(const double* y, const double* y5, const double* err,
                                            double rtol, double atol) {
@@ -157,7 +158,7 @@ __device__ __forceinline__ double err_norm(const double* y, const double* y5, co
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     const double sc = fma(rtol, nnmax(absd(y[c]), absd(y5[c])), atol);
-    const double r = absd(absd(err[c]) * rcp_nr(sc));
+    const double r = absd(absd(err[c]) * rcp_fx(sc));
     E = nnmax(E, r);
   }
   return E;
@@ -172,7 +173,7 @@ __device__ __forceinline__ bool accept(double E) { return nnbits(E) <= nnbits(1.
 __device__ __forceinline__ double step_factor(double E) {
   if (nnbits(E) > nnbits(__longlong_as_double(0x7ff0000000000000LL))) return 0.2;  // NaN
   const double Ec = nnmin(nnmax(E, 1e-4), 2000.0);
-  const double fac = 0.9 * inv_fifth_root(Ec);
+  const double fac = 0.9 * inv_fifth_root_fx(Ec);
   return nnmin(nnmax(fac, 0.2), 5.0);
 }
 

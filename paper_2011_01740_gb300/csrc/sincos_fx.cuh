@@ -29,52 +29,10 @@
 // __host__ __device__ so that the host can test it.
 #pragma once
 
-#include <cstdint>
-
-#ifndef __CUDACC__
-#define __host__
-#define __device__
-#define __forceinline__ inline
-#endif
+#include "fixed64.cuh"
 
 namespace ens {
 namespace fx {
-
-__host__ __device__ __forceinline__ uint64_t mulhi(uint64_t a, uint64_t b) {
-#ifdef __CUDA_ARCH__
-  return __umul64hi(a, b);
-#else
-  return (uint64_t)(((unsigned __int128)a * b) >> 64);
-#endif
-}
-
-__host__ __device__ __forceinline__ int clz64(uint64_t x) {  // x != 0
-#ifdef __CUDA_ARCH__
-  return __clzll((long long)x);
-#else
-  return __builtin_clzll(x);
-#endif
-}
-
-__host__ __device__ __forceinline__ uint64_t dbits(double x) {
-#ifdef __CUDA_ARCH__
-  return (uint64_t)__double_as_longlong(x);
-#else
-  uint64_t b;
-  __builtin_memcpy(&b, &x, 8);
-  return b;
-#endif
-}
-
-__host__ __device__ __forceinline__ double from_bits(uint64_t b) {
-#ifdef __CUDA_ARCH__
-  return __longlong_as_double((long long)b);
-#else
-  double x;
-  __builtin_memcpy(&x, &b, 8);
-  return x;
-#endif
-}
 
 // round(x 2^64) mod 2^64 (ties up) for finite x: x = m 2^(e-52) with the
 // 53-bit integer m, so x 2^64 = m 2^s, s = e + 12; bits at or above 2^64 are
