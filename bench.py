@@ -46,7 +46,7 @@ FLOPS_FP64_FORM_KM_TRIAL = 589.91
 # DRAM bytes (read + write) of one benchmarked Keller-Miksis launch, from the
 # one-pass ncu capture in profiles/ (inputs 15.7 MB read once, 134 MB of
 # per-period accessories written once); None once the kernel changes.
-KM_LAUNCH_DRAM_BYTES = 37872128 + 117764864
+KM_LAUNCH_DRAM_BYTES = 40354816 + 120015104
 FLOPS_PER_X2P_STEP = 21.0     # 10 DFMA + 1 DADD (Sec. 3.2.2 counters; kernel counted by ncu)
 FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast kernel
 # executed flops per trial of the other adaptive kernels (ncu counts,
@@ -1040,7 +1040,7 @@ def run_profile_case(case: str):
                            n_phases=t.n_phases, phase_len=t.phase_len)
         ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
                              ens.ENS_RKCK45, tol)
-        ens.ens_set_launch(ctx, ens.make_launch(block=160, blocks_per_sm=1, cost_order=1))
+        ens.ens_set_launch(ctx, ens.make_launch(block=192, blocks_per_sm=1, cost_order=1))
     elif case == "km_full2":
         # all 131,044 systems, 2 periods: the instruction mix of the benchmarked kernel
         km = km_slice(1, 0, n_phases=2)
@@ -1209,7 +1209,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--phases", type=int, default=64)
-    ap.add_argument("--block", type=int, default=160)
+    ap.add_argument("--block", type=int, default=192)
     ap.add_argument("--bps", type=int, default=1)
     ap.add_argument("--cost-order", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)

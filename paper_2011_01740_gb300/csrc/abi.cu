@@ -345,6 +345,10 @@ ens_status enqueue_solve(ens_ctx* c, const ens_launch& L, cudaStream_t s, double
     a.order = c->order;
   }
   AdaptLaunch AL = adapt_launch(c, L);
+  // the phase-mode FP64 and tangent kernels rank the first claims by
+  // sub-partition when one block runs per SM
+  a.first_by_subpartition = a.persistent && a.order && a.n_phases > 0 && L.blocks_per_sm == 1 &&
+                            spt_of(L) == 1 && (c->tol.prec == ENS_FP64 || c->tol.prec == ENS_FP64_STRICT);
   ENS_CUDA(c, record_kernel_event(c, 0, s));
   cudaError_t e = launch_adaptive(c, a, AL, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "adaptive launch");

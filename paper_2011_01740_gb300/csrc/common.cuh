@@ -104,6 +104,10 @@ struct AdaptArgs {
   int32_t persistent;
   int32_t pair;          // kCashKarp or kDormandPrince
   uint64_t timeout_ns;
+  // phase mode, persistent, longest-first, one block per SM: the first claims
+  // go to the lanes of warps that own their sub-partition first (see
+  // claim_first_by_subpartition); 0 elsewhere
+  int32_t first_by_subpartition;
 };
 
 // Grid of an adaptive launch.

@@ -190,6 +190,33 @@ __device__ __forceinline__ int64_t claim(const AdaptArgs& a, bool first) {
   return a.order ? (int64_t)a.order[k] : (int64_t)k;
 }
 
+// First claim of a lane in a persistent, longest-first launch with one block
+// per SM, deterministic and aware of the sub-partitions: warp w of a block
+// runs on sub-partition w mod 4, and a warp that shares its sub-partition
+// gets about half of that sub-partition's FP64 pipe.  The lanes of warps that
+// own their sub-partition take the first ranks of the claim order (the
+// longest systems), the others the next ones; later claims continue from rank
+// gridDim.x * blockDim.x in order (claim_next_after_ranked).  The claim order
+// never changes what a system computes.
+__device__ __forceinline__ int64_t claim_first_by_subpartition(const AdaptArgs& a) {
+  const int W = (int)(blockDim.x >> 5), w = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  int u_total = 0, u_before = 0;
+  for (int x = 0; x < W; ++x) {
+    const bool own = ((W - (x & 3) + 3) >> 2) == 1;  // the only warp of block x's sub-partition
+    u_total += own;
+    u_before += own && x < w;
+  }
+  const bool own = ((W - (w & 3) + 3) >> 2) == 1;
+  const int64_t U = (int64_t)gridDim.x * u_total * 32;
+  const int64_t rank = own ? ((int64_t)blockIdx.x * u_total + u_before) * 32 + lane
+                           : U + ((int64_t)blockIdx.x * (W - u_total) + (w - u_before)) * 32 + lane;
+  return rank < a.n ? (int64_t)a.order[rank] : -1;
+}
+__device__ __forceinline__ int64_t claim_next_after_ranked(const AdaptArgs& a) {
+  const unsigned long long k = (unsigned long long)gridDim.x * blockDim.x + atomicAdd(&a.scratch->next, 1ULL);
+  return k < (unsigned long long)a.n ? (int64_t)a.order[k] : -1;
+}
+
 // ---------------------------------------------------------------------------
 // Phase mode (Keller-Miksis, Sec. 4.2): n_phases integrations over
 // tau in [t0, t0 + phase_len] with tau reset at each phase start; running max
@@ -202,7 +229,7 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
   constexpr int D = Sys::kDim;
   const double tau_end = a.t0 + a.phase_len;
   const uint64_t deadline = global_ns() + a.timeout_ns;
-  int64_t i = claim(a, true);
+  int64_t i = a.first_by_subpartition ? claim_first_by_subpartition(a) : claim(a, true);
   bool timed_out = false;
   Sys s;
   // drive at the phase start (tau = t0), at the current tau, and at tau + h
@@ -329,7 +356,7 @@ __global__ void __launch_bounds__(256) ck_phased_kernel(AdaptArgs a) {
     }
     if (sys_done) {
       finish_system(i);
-      i = claim(a, false);
+      i = a.first_by_subpartition ? claim_next_after_ranked(a) : claim(a, false);
       if (i >= 0) start_system(i);
     }
   }

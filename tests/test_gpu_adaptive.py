@@ -117,6 +117,24 @@ def test_persistent_refill_solves_every_system_as_the_plain_launch():
             assert np.array_equal(g[k], ref[k], equal_nan=True), (k, L.as_dict())
 
 
+@pytest.mark.parametrize("block", [160, 192, 224])
+@pytest.mark.parametrize("m", [(19, 23), (3, 40), (150, 200)])
+def test_first_claims_by_subpartition_cover_every_system_once(block, m):
+    """Persistent, longest-first, one block per SM: the first claims are ranked
+    by sub-partition (lanes of warps that own theirs first), later ones
+    continue from the counter.  With 120, 437 and 30,000 systems (fewer
+    systems than the unshared lanes, between them and all lanes, and many
+    refills) every system is solved once and comes out bitwise as in the
+    plain launch."""
+    km = W.km(*m, n_phases=2)
+    ref = _km_gpu(km, launch=ens.make_launch(mode=ens.ENS_LAUNCH_PLAIN, block=128))
+    g = _km_gpu(km, launch=ens.make_launch(mode=ens.ENS_LAUNCH_PERSISTENT, block=block, blocks_per_sm=1,
+                                           cost_order=1))
+    assert g["sync"] == ens.ENS_OK and np.all(g["nacc"] > 0)
+    for k in ("y", "acc", "nacc", "nrej", "nrhs", "status", "dt"):
+        assert np.array_equal(g[k], ref[k], equal_nan=True), k
+
+
 @pytest.mark.parametrize("prec", [ens.ENS_FP64, ens.ENS_FP32_COMP])
 def test_transient_phases_are_integrated_but_not_recorded(prec):
     """n_transient = 5 of 8 phases: the recorded rows are the last 3 phases of
