@@ -51,7 +51,10 @@ FLOPS_PER_X2P_STEP = 21.0     # 10 DFMA + 1 DADD (Sec. 3.2.2 counters; kernel co
 FLOPS_PER_LORENZ_STEP = 75.0  # 30 DFMA + 8 DMUL + 7 DADD per step of the fast kernel
 # executed flops per trial of the other adaptive kernels (ncu counts,
 # profiles/; None until measured: their fractions are then null)
-FLOPS_PER_VALVE_TRIAL = 273.36        # FP64: 102.92 DFMA + 53.42 DMUL + 14.10 DADD, ck_events_kernel
+FLOPS_PER_VALVE_TRIAL = 219.10        # FP64: 84.83 DFMA + 35.34 DMUL + 14.10 DADD, ck_events_kernel
+# the valve trial in its all-FP64 form (square root, fifth root and reciprocals
+# as FP64 arithmetic: 115.0 DFMA + 57.5 DMUL + 14.1 DADD, profiles/)
+FLOPS_FP64_FORM_VALVE_TRIAL = 301.59
 FLOPS_FP32_PER_FP32C_TRIAL = 1516.0   # FP32: 441.1 FFMA + 162.4 FMUL + 471.4 FADD, ck_phased_fp32c_kernel
 FLOPS_FP32_PER_DF_TRIAL = 5277.6      # FP32: 746.1 FFMA + 454.9 FMUL + 3330.5 FADD, ck_phased_df_kernel
 FLOPS_FP32_PER_DF_VALVE_TRIAL = 3173.5  # FP32, ck_events_df_kernel
@@ -402,6 +405,7 @@ def configs_summary(value, roofline, sec, n_headline):
     v = sec.get("relief_valve_262144")
     if v:
         out["c3_valve_262144_fp64"] = {"value": _r(v["value"]), "s": _r(v["ms"] / 1e3), "frac": _r(v.get("fp64_frac"), 3),
+                                       "form_frac": _r(v.get("fp64_form_frac"), 3),
                                        "launch": _shape(v["launch"]), "parity": "events exact, acc <=1e-8"}
         if v.get("fp32x2"):
             out["c3_valve_262144_fp64"]["df"] = _r({k: v["fp32x2"][k] for k in ("s", "speedup", "err_p99", "fp32_frac")},
@@ -881,7 +885,8 @@ def run_secondary(ens, torch, stream, dev, tuned=True):
                                   "unit": "system-steps/s", "trials": trials, "launch": L.as_dict(), "tune_s": tune_s,
                                   "tune_table": valve_table,
                                   "fp64_frac": (FLOPS_PER_VALVE_TRIAL * trials / (kms / 1e3) / FP64_PEAK
-                                                if FLOPS_PER_VALVE_TRIAL else None)}
+                                                if FLOPS_PER_VALVE_TRIAL else None),
+                                  "fp64_form_frac": FLOPS_FP64_FORM_VALVE_TRIAL * trials / (kms / 1e3) / FP64_PEAK}
     # the same sweep in double-float arithmetic (state, stages, right-hand
     # side and controller as float pairs; time, events, impact law and
     # sticking in FP64): speedup, event counts and value rows against FP64

@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "fifth_root_fx.cuh"
 #include "sincos_fx.cuh"
+#include "sqrt_fx.cuh"
 
 namespace ens {
 
@@ -123,23 +124,6 @@ __device__ __forceinline__ double rcp_nr(double d) {
   return fma(fma(e, e, e), v, v);
 }
 
-// sqrt(x) for x >= 0: the hardware reciprocal square root
-// approximation (PTX rsqrt.approx.ftz.f64) refined by one third-order
-// Newton-Raphson step for 1/sqrt(x), r (1 + e/2 + 3 e^2/8) with e = 1 - x r^2
-// (the binomial series of (1 - e)^(-1/2)), which cubes the seed's relative
-// error; then sqrt(x) = x r.  Within about 2 ulp, not correctly rounded;
-// 7 FP64 instructions after the seed against about 9 for sqrt().
-__device__ __forceinline__ double sqrt_nr(double x) {
-  // zero, subnormal (the seed flushes them), infinite and NaN x take the
-  // library square root; the range test is one unsigned compare on the high
-  // word (normal positive doubles have 0x00100000 <= hi < 0x7ff00000)
-  if ((unsigned)__double2hiint(x) - 0x00100000u >= 0x7fe00000u) return sqrt(x);
-  double r;
-  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  const double e = fma(-x, r * r, 1.0);
-  const double rr = fma(r * e, fma(0.375, e, 0.5), r);
-  return x * rr;
-}
 
 // sin(2 pi x) and cos(2 pi x) together for |x| < 2^49, in FP64 arithmetic.
 // The argument is split exactly as x = k/4 + r with k the nearest integer to
@@ -297,7 +281,8 @@ struct KellerMiksis {
 // Pressure relief valve (Sec. 4.3, Eqs. pressure_relief_valve_1-3):
 //   y1' = y2, y2' = -kappa y2 - (y1 + delta) + y3, y3' = beta (q - y1 sqrt(y3)).
 // sqrt is taken of max(y3, 0): y3 >= 0 for q > 0, the clamp only keeps a
-// rounding excursion from producing a NaN; it is sqrt_nr (about 2 ulp).  The
+// rounding excursion from producing a NaN; it is sqrt_fx (refined in fixed
+// point on the integer pipe, within half an ulp plus 2^-58).  The
 // clamp tests the sign bit on the integer pipe (negative values and -0 give
 // +0), which spares the FP64 pipe a min / max per evaluation.
 // ---------------------------------------------------------------------------
@@ -318,7 +303,7 @@ struct ReliefValve {
     dy[0] = y[1];
     dy[1] = fma(-kappa, y[1], y[2] - (y[0] + delta));
     const double y3 = __double2hiint(y[2]) < 0 ? 0.0 : y[2];
-    dy[2] = beta * fma(-y[0], sqrt_nr(y3), q);
+    dy[2] = beta * fma(-y[0], sqrt_fx(y3), q);
   }
   using Drive = NoDrive;
   __device__ __forceinline__ Drive drive(double) const { return {}; }
