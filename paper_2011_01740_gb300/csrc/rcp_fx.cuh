@@ -39,23 +39,40 @@ __host__ __device__ __forceinline__ float rcp_split(uint64_t b) {
 #endif
 }
 
-// the refinement of the seed vf of 1/m and the result (1/m) 2^(-e) with the
-// sign of d, as a double
-__host__ __device__ __forceinline__ double rcp_refine(uint64_t b, float vf) {
+// the refinement of the seed vf of 1/m for the 53-bit significand mn of m
+// (implicit bit set): 1/m x 2^62 in (2^61, 2^62]
+__host__ __device__ __forceinline__ uint64_t rcp_fixed(uint64_t mn, float vf) {
 #ifdef __CUDA_ARCH__
   const unsigned vb = __float_as_uint(vf);
 #else
   unsigned vb;
   __builtin_memcpy(&vb, &vf, 4);
 #endif
-  const int e = (int)((b >> 52) & 0x7ff) - 1023;
   // v x 2^62 from the float's bits (exact)
   const int ev = (int)((vb >> 23) & 0xffu) - 127;
   const uint64_t V = (uint64_t)((vb & 0x7fffffu) | 0x800000u) << ((39 + ev) & 63);
-  const uint64_t M = ((b & 0x000fffffffffffffull) | 0x0010000000000000ull) << 10;  // m x 2^62
-  const int64_t S = (int64_t)((1ull << 62) - (mulhi(M, V) << 2));  // s = 1 - m v, x 2^62
-  const int64_t S2 = (int64_t)((uint64_t)smulhi(S, S) << 2);        // s^2 x 2^62
-  const uint64_t W = V + ((uint64_t)smulhi((int64_t)V, S + S2) << 2);  // 1/m x 2^62 in (2^61, 2^62]
+  const uint64_t M = mn << 10;                                        // m x 2^62
+  const int64_t S = (int64_t)((1ull << 62) - (mulhi(M, V) << 2));    // s = 1 - m v, x 2^62
+  const int64_t S2 = (int64_t)((uint64_t)smulhi(S, S) << 2);          // s^2 x 2^62
+  return V + ((uint64_t)smulhi((int64_t)V, S + S2) << 2);
+}
+
+// the float seed of 1/m
+__host__ __device__ __forceinline__ float rcp_seed(float mf) {
+#ifdef __CUDA_ARCH__
+  float vf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(vf) : "f"(mf));
+  return vf;
+#else
+  return 1.0f / mf;
+#endif
+}
+
+// the refinement of the seed vf of 1/m and the result (1/m) 2^(-e) with the
+// sign of d, as a double
+__host__ __device__ __forceinline__ double rcp_refine(uint64_t b, float vf) {
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  const uint64_t W = rcp_fixed((b & 0x000fffffffffffffull) | 0x0010000000000000ull, vf);
   const int lz = clz64(W);
   const uint64_t nrm = W << lz;
   uint64_t m53 = nrm >> 11;
@@ -71,14 +88,7 @@ __host__ __device__ __forceinline__ double rcp_refine(uint64_t b, float vf) {
 __host__ __device__ __forceinline__ double rcp_fx(double d) {
   using namespace fx;
   const uint64_t b = dbits(d);
-  const float mf = rcp_split(b);
-#ifdef __CUDA_ARCH__
-  float vf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(vf) : "f"(mf));
-#else
-  const float vf = 1.0f / mf;
-#endif
-  const double r = rcp_refine(b, vf);
+  const double r = rcp_refine(b, rcp_seed(rcp_split(b)));
   const unsigned ef = (unsigned)((b >> 52) & 0x7ff);
   const bool ok = ef != 0 && ef < 0x7fd;  // normal, and 1/d normal (|d| < 2^1022)
   return ok ? r : from_bits(0x7ff8000000000000ull);
