@@ -578,7 +578,7 @@ def run_screen(ens, torch, stream, dev, ctx, km, solve_ms, solve_steps, args):
     x, y = screen.training_set_from_acc(ens, km, acc, rows // 2, rows // 4, dev, stream)
     r = screen.run(ens, screen_m=args.screen_m, n_phases=rows // 2, first_phase=rows // 4, threshold=0.05,
                    bound=args.screen_bound, calib_points=16384, val_stride=4, epochs=args.screen_epochs,
-                   batch=1024, stream=stream, train=(x, y, solve_ms / 1e3, solve_steps),
+                   batch=args.screen_batch, lr=args.screen_lr, stream=stream, train=(x, y, solve_ms / 1e3, solve_steps),
                    fallback_launch=ens.ens_get_launch(ctx))
     r["screen_grid"] = [args.screen_m, args.screen_m]
     # screened scan throughput: grid points per second of screen + FP64 fallback
@@ -1222,7 +1222,11 @@ def main():
     ap.add_argument("--ref-systems", type=int, default=1024)
     ap.add_argument("--quick", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--screen-m", type=int, default=4096, help="screening grid side (4096 x 4096 = 16.8M points)")
-    ap.add_argument("--screen-epochs", type=int, default=150)
+    # training length and batch of the surrogate: 2,400 epochs of 8,192 samples (10 s) leave 1.6 % of the
+    # 4096^2 grid to the FP64 fallback at the p99 bound; 150 epochs of 1,024 (1.9 s) left 16 %
+    ap.add_argument("--screen-epochs", type=int, default=2400)
+    ap.add_argument("--screen-batch", type=int, default=8192)
+    ap.add_argument("--screen-lr", type=float, default=6e-3)
     ap.add_argument("--screen-bound", type=float, default=0.05,
                     help="unflagged p99 |ln r error| the screening gate is calibrated for")
     ap.add_argument("--no-tune", action="store_true", help="hand-measured launch shapes instead of ens_autotune")

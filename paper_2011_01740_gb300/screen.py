@@ -119,7 +119,7 @@ def calibrate_gradient_gate(err: np.ndarray, sd: np.ndarray, g: np.ndarray, spre
 
 def run(ens, train_shape=(362, 362), screen_m=1024, n_phases=64, first_phase=32, threshold=0.05,
         bound=0.05, quantile=99.0, calib_points=16384, val_stride=4, slope_spacing=2.0 / 1023, members=4,
-        epochs=150, batch=1024, lr=2e-3, lr_final=2e-5, seed=W.SEED, stream=None, liquid=None, train=None,
+        epochs=2400, batch=8192, lr=6e-3, lr_final=2e-5, seed=W.SEED, stream=None, liquid=None, train=None,
         fallback_launch=None):
     """Train on a train_shape grid, calibrate the fallback gate, screen a
     screen_m x screen_m log grid, re-solve the flagged points, validate on the

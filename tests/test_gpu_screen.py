@@ -24,7 +24,7 @@ def test_screened_scan_small():
     import torch
     assert torch.cuda.is_available()
     r = screen.run(ens, train_shape=(96, 96), screen_m=256, n_phases=16, first_phase=8, threshold=0.05,
-                   bound=BOUND, quantile=QUANTILE, calib_points=4096, val_stride=2, epochs=80, batch=512)
+                   bound=BOUND, quantile=QUANTILE, calib_points=4096, val_stride=2, epochs=80, batch=512, lr=2e-3)
     print({k: v for k, v in r.items()})
     assert r["train_loss_first_last"][1] < 0.5 * r["train_loss_first_last"][0]
     assert 0.0 < r["fallback_fraction"] < 1.0
