@@ -34,6 +34,7 @@
 // the float pair holds exactly.  Near equilibrium the float error then scales
 // with |y1 - 1| instead of with C0.
 #include "common.cuh"
+#include "fcmp.cuh"
 #include "rhs.cuh"
 
 namespace ens {
@@ -147,6 +148,31 @@ __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi 
 
 __device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)a.lo; }
 
+// Exact conversions between double and float on the integer pipe: a
+// conversion instruction costs an FP64 pipe slot on this part.
+//   to_d:   float -> double, exact for zero and normal floats (a subnormal
+//           float becomes a double of about the same, tiny size; the
+//           acceptance test below compares such values against atol);
+//   rn_f32: double -> float rounded to nearest, ties to even, as the
+//           conversion instruction rounds, for zero and |x| in
+//           [2^-126, 2^128) (the step, its low part and the time here).
+__device__ __forceinline__ double to_d(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned sign = b & 0x80000000u, mag = b & 0x7fffffffu;
+  const unsigned hi = mag == 0 ? sign : (((mag >> 3) + ((1023u - 127u) << 20)) | sign);
+  return __hiloint2double((int)hi, (int)(mag << 29));
+}
+__device__ __forceinline__ float rn_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long mag = b & 0x7fffffffffffffffull;
+  const unsigned long long r = mag - ((unsigned long long)(1023 - 127) << 52);  // exponent rebiased
+  const unsigned q = (unsigned)(r >> 29);                                     // exponent and 23 bits
+  const unsigned rest = (unsigned)(r & 0x1fffffffu);
+  const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (q & 1u))) ? 1u : 0u;
+  return __uint_as_float(mag == 0 ? sign : ((q + up) | sign));  // a carry steps the exponent
+}
+
 // y + h * sum  with y a float pair, h = hh + hl a float pair, sum = s + c
 __device__ __forceinline__ ff ff_axpy(ff y, float hh, float hl, float s, float c) {
   const float p = hh * s;
@@ -234,15 +260,16 @@ __global__ void __launch_bounds__(256) ck_phased_fp32c_kernel(AdaptArgs a) {
     } else {
       double h = dt;
       bool clamped = false;
-      if (h >= tau_end - tau) {
-        h = tau_end - tau;
+      const double rest = tau_end - tau;  // > 0 inside a phase
+      if (nnbits(h) >= nnbits(rest)) {
+        h = rest;
         clamped = true;
       }
-      const float hh = (float)h, hl = (float)(h - (double)hh);
+      const float hh = rn_f32(h), hl = rn_f32(h - to_d(hh));
       // deviation of the stage base: x0 = (y1 - 1) exactly as a float sum
       const float xb = (y0v.hi - 1.0f) + y0v.lo;
       const float vb = y1v.hi + y1v.lo;
-      const float t2 = (float)(2.0 * tau), h2 = 2.0f * hh;
+      const float t2 = 2.0f * rn_f32(tau), h2 = 2.0f * hh;  // 2 RN(tau) = RN(2 tau)
       if (!k1valid) {
         k1x = vb;
         k1v = s.f(xb, vb, t2);
@@ -293,9 +320,10 @@ __global__ void __launch_bounds__(256) ck_phased_fp32c_kernel(AdaptArgs a) {
       // the states, so ten FP64 instructions decide the step.
       const float exv = ex.value(), evv = ev.value();
       const float m0 = fmaxf(fabsf(y0v.hi), fabsf(n0.hi)), m1 = fmaxf(fabsf(y1v.hi), fabsf(n1.hi));
-      const double e0 = fabs(h * (double)exv), e1 = fabs(h * (double)evv);
-      const double sc0 = fma(a.rtol, (double)m0, a.atol), sc1 = fma(a.rtol, (double)m1, a.atol);
-      const bool accept = (e0 <= sc0) && (e1 <= sc1);
+      const double e0 = absd(h * to_d(exv)), e1 = absd(h * to_d(evv));
+      const double sc0 = fma(a.rtol, to_d(m0), a.atol), sc1 = fma(a.rtol, to_d(m1), a.atol);
+      // e <= sc on the bit patterns (e >= +0 or NaN, sc > 0): false for NaN
+      const bool accept = nnbits(e0) <= nnbits(sc0) && nnbits(e1) <= nnbits(sc1);
       // step factor from the float ratio E = max_i |err_i| / sc_i
       const float E = fmaxf(__fdividef(fabsf(hh * exv), fmaf(rtol_f, m0, atol_f)),
                             __fdividef(fabsf(hh * evv), fmaf(rtol_f, m1, atol_f)));
@@ -317,12 +345,8 @@ __global__ void __launch_bounds__(256) ck_phased_fp32c_kernel(AdaptArgs a) {
         ++nacc;
         if (ff_gt(y0v, ymax)) ymax = y0v;
         if (ff_gt(ymin, y0v)) ymin = y0v;
-        if (!clamped) {
-          dt = h * (double)fac;
-          dt = dt > a.dt_max ? a.dt_max : dt;
-          dt = dt < a.dt_min ? a.dt_min : dt;
-        }
-        if (!(tau < tau_end)) {
+        if (!clamped) dt = bounded_step(h, to_d(fac), a.dt_min, a.dt_max);
+        if (okey(tau) >= okey(tau_end)) {  // !(tau < tau_end)
           if (ph >= a.n_transient) {
             a.acc[(int64_t)(2 * (ph - a.n_transient)) * a.n + i] = ff_to_d(ymax);
             a.acc[(int64_t)(2 * (ph - a.n_transient) + 1) * a.n + i] = ff_to_d(ymin);
@@ -337,8 +361,8 @@ __global__ void __launch_bounds__(256) ck_phased_fp32c_kernel(AdaptArgs a) {
         }
       } else {
         ++nrej;
-        dt = h * (double)fac;
-        if (dt < a.dt_min) st |= kStDtUnderflow;
+        dt = h * to_d(fac);
+        if (nnbits(dt) < nnbits(a.dt_min)) st |= kStDtUnderflow;
       }
     }
     if (sys_done) {
