@@ -210,8 +210,40 @@ __host__ __device__ __forceinline__ double widen(float v) {
   return d;
 #endif
 }
-// double -> double-word: one FP64 subtraction, the rest integer and FP32
+// double -> double-word on the integer pipe: hi = trunc_f(x), and lo the
+// exact remainder x - hi, which is the 29 low significand bits of x, cut to
+// their leading 24 bits as trunc_f cuts it (0 below 2^-100).  This is the
+// pair that trunc_f(x - widen(hi)) gives, without that FP64 subtraction
+// (tests/test_df_host.py compares the two bit for bit).
 __host__ __device__ __forceinline__ DF from_double(double x) {
+  const float h = trunc_f(x);
+#ifdef __CUDA_ARCH__
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long u;
+  __builtin_memcpy(&u, &x, 8);
+#endif
+  const int ef = (int)((u >> 52) & 0x7ff);
+  const unsigned long long L = u & 0x1fffffffull;  // x - hi = L 2^(ef - 1075)
+#ifdef __CUDA_ARCH__
+  const int p = 63 - __clzll((long long)(L | 1ull));  // leading bit of L (0..28)
+#else
+  const int p = 63 - __builtin_clzll(L | 1ull);
+#endif
+  const int e_low = ef - 1075 + p;                     // exponent of the remainder
+  const unsigned frac = (unsigned)(((L << (63 - p)) << 1) >> 41);  // its next 23 bits, truncated
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const unsigned lb = (L == 0 || e_low < -100) ? 0u : ((((unsigned)(e_low + 127) << 23) | frac) | sign);
+#ifdef __CUDA_ARCH__
+  const float l = __uint_as_float(lb);
+#else
+  float l;
+  __builtin_memcpy(&l, &lb, 4);
+#endif
+  return fast_two_sum(h, l);
+}
+// the same pair through one FP64 subtraction (the reference for the test)
+__host__ __device__ __forceinline__ DF from_double_sub(double x) {
   const float h = trunc_f(x);
   const float l = trunc_f(x - widen(h));
   return fast_two_sum(h, l);

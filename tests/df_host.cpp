@@ -44,4 +44,15 @@ void prims(int n, const double* a, const double* b, double* out) {
     out[5 * n + i] = to_double(sub(x, y));
   }
 }
+// the integer double -> pair split against the FP64-subtraction form: hi and lo
+// floats of both (out [4][n]: hi, lo, hi_ref, lo_ref)
+void split_df(int n, const double* x, float* out) {
+  for (int i = 0; i < n; ++i) {
+    const DF a = from_double(x[i]), b = from_double_sub(x[i]);
+    out[i] = a.hi;
+    out[n + i] = a.lo;
+    out[2 * n + i] = b.hi;
+    out[3 * n + i] = b.lo;
+  }
+}
 }

@@ -147,3 +147,19 @@ def test_dekker_addition_error_is_bounded_by_the_operands(lib):
     lib.add_terms_df(n, _p(a), _p(b), out.ctypes.data_as(P))
     err = np.abs(out - (xa + xb)) / (np.abs(xa) + np.abs(xb))
     assert err.max() <= 2.0 * U2, err.max() / U2
+
+
+def test_integer_split_equals_the_subtraction_form_bit_for_bit(lib):
+    """from_double takes the low part from the significand bits (integer
+    pipe); it must give exactly the pair of the FP64-subtraction form, over
+    magnitudes from 2^-120 to 2^120, both signs, exact floats, zero."""
+    rng = np.random.default_rng(21)
+    x = np.concatenate([rng.choice([-1.0, 1.0], 20000) * 2.0 ** rng.uniform(-120, 120, 20000),
+                        rng.uniform(-3.0, 3.0, 5000), [0.0, -0.0, 1.0, -1.5, 2.0 ** -100, 2.0 ** -101,
+                                                         np.float32(0.1).astype(np.float64), 1.0 + 2.0 ** -52]])
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(4 * x.size, dtype=np.float32)
+    lib.split_df(x.size, x.ctypes.data_as(P), out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    o = out.reshape(4, x.size)
+    assert np.array_equal(o[0].view(np.uint32), o[2].view(np.uint32))
+    assert np.array_equal(o[1].view(np.uint32), o[3].view(np.uint32))
