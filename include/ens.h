@@ -293,8 +293,11 @@ int32_t ens_npar(const ens_ctx *ctx);
  *   1/8 of the phases (or of the time span) of every system -- the horizon is
  *   cut, not the ensemble, so the balance between throughput and the
  *   longest system's chain stays that of the full solve; the fraction is
- *   halved while one shortened solve takes over 0.6 s.  The claim order
- *   comes from the full solve's one-phase pilot, computed once.
+ *   halved while one shortened solve takes over 0.6 s.  The two fastest
+ *   candidates are then timed again on twice that horizon (rows with the
+ *   doubled horizon_frac), and the faster of those two is the choice: shapes
+ *   with different tails can trade places as the horizon grows.  The claim
+ *   order comes from the full solve's one-phase pilot, computed once.
  * The context's outputs hold the last candidate's shortened solve afterwards.
  * The choice and its table are cached per (system, solver, precision, n,
  * phases, transient phases, horizon, device) for the process. */

@@ -835,6 +835,20 @@ ens_status ens_autotune(ens_ctx* c, void* stream, ens_launch* best) {
       if (st == ENS_OK && spt2_static_ok(c, L2) && !(c->km_flags & (kKmDual | kKmGeneralExponent)))
         st = consider(L2);
     }
+    // The two fastest candidates again on twice the horizon, and the faster
+    // of those is the choice: shapes whose tails differ (a plain launch waits
+    // for the longest system of every block, a persistent one refills its
+    // lanes) can trade places as the horizon grows, and on the 1024 x 1024
+    // double-float grid a plain launch that led on 1/32 of the horizon took
+    // 12.8 s against 10.0 s for the persistent shape on the whole solve.
+    if (st == ENS_OK && frac < 1.0 && c->tune_rows.size() >= 2) {
+      std::vector<ens_tune_row> ranked(c->tune_rows.begin(), c->tune_rows.end());
+      std::stable_sort(ranked.begin(), ranked.end(),
+                       [](const ens_tune_row& x, const ens_tune_row& y) { return x.ms < y.ms; });
+      frac = std::min(1.0, 2.0 * frac);
+      best_ms = 1e30f;
+      for (int r = 0; r < 2 && st == ENS_OK; ++r) st = consider(ranked[r].launch);
+    }
     c->order_ready = false;
   }
   if (st != ENS_OK) return st;

@@ -349,9 +349,10 @@ def test_autotune_of_the_adaptive_solve():
     """The tuner times persistent launches of 3-24 warps per SM with
     longest-first claiming, the best residency without it, a plain launch and
     two systems per thread at 6 and 8 warps per SM, on a shortened horizon of
-    every system (1/8 of 16 phases), keeps the fastest, and leaves results
-    unchanged: the claim order and the launch shape never change what a
-    system computes."""
+    every system (1/8 of 16 phases), times the two fastest again on twice
+    that horizon, keeps the faster of those, and leaves results unchanged:
+    the claim order and the launch shape never change what a system
+    computes."""
     km = W.km(24, 20, n_phases=16)
     C = km_coeffs_lib(km["phys"], km["liquid"])
     ctx = ens.ens_create(ens.ENS_SYS_KELLER_MIKSIS, C.shape[1], C, km["y0"], (0.0, 1.0),
@@ -362,15 +363,20 @@ def test_autotune_of_the_adaptive_solve():
         ref = {w: ens.ens_read(ctx, w) for w in (ens.ENS_ACC, ens.ENS_STATE, ens.ENS_NSTEPS)}
         best = ens.ens_autotune(ctx)
         rows = ens.ens_autotune_table(ctx)
-        assert len(rows) == 13
-        assert all(r["horizon_frac"] == 0.125 for r in rows)
+        # 13 candidates on 1/8 of the horizon, then the two fastest again on 1/4
+        assert len(rows) == 15
+        assert all(r["horizon_frac"] == 0.125 for r in rows[:13])
+        assert all(r["horizon_frac"] == 0.25 for r in rows[13:])
+        first = sorted(rows[:13], key=lambda r: r["ms"])[:2]
+        assert [r["launch"] for r in rows[13:]] == [r["launch"] for r in first]
+        rows, confirm = rows[:13], rows[13:]
         persistent = [r for r in rows if r["launch"]["mode"] == ens.ENS_LAUNCH_PERSISTENT]
         warps = lambda rs: {r["launch"]["block"] // 32 * r["launch"]["blocks_per_sm"] for r in rs}
         assert warps(r for r in persistent if r["launch"]["systems_per_thread"] == 1) == {3, 4, 5, 6, 7, 8, 12, 16, 24}
         assert warps(r for r in persistent if r["launch"]["systems_per_thread"] == 2) == {6, 8}
         assert any(r["launch"]["mode"] == ens.ENS_LAUNCH_PLAIN for r in rows)
         assert any(r["launch"]["cost_order"] == 0 for r in persistent)
-        fastest = min(rows, key=lambda r: r["ms"])["launch"]
+        fastest = min(confirm, key=lambda r: r["ms"])["launch"]
         assert (fastest["mode"], fastest["block"], fastest["blocks_per_sm"], fastest["cost_order"],
                 fastest["systems_per_thread"]) == \
             (best.mode, best.block, best.blocks_per_sm, best.cost_order, max(1, best.systems_per_thread))
@@ -381,7 +387,7 @@ def test_autotune_of_the_adaptive_solve():
         # a second call returns the cached choice and table
         again = ens.ens_autotune(ctx)
         assert (again.block, again.blocks_per_sm) == (best.block, best.blocks_per_sm)
-        assert len(ens.ens_autotune_table(ctx)) == len(rows)
+        assert len(ens.ens_autotune_table(ctx)) == len(rows) + len(confirm)
     finally:
         ens.ens_destroy(ctx)
 
