@@ -47,11 +47,6 @@ __device__ __forceinline__ Dual rcp_nr(Dual x) {
   const double r = rcp_nr(x.v);
   return {r, -(r * r) * x.d};
 }
-// (x^(-1/5))' = -(1/5) x^(-1/5) x' / x
-__device__ __forceinline__ Dual inv_fifth_root_fx(Dual x) {
-  const double r = inv_fifth_root_fx(x.v);
-  return {r, -0.2 * r * x.d / x.v};
-}
 // g = y1^(-21/5): the value from the same fixed-point evaluation as the
 // plain right-hand side (so the tangent system's state part stays bitwise
 // that of KellerMiksis), g' = -(21/5) g y1' / y1 with rx = 1/y1

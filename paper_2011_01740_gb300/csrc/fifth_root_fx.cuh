@@ -2,10 +2,10 @@
 //
 // The Keller-Miksis right-hand side needs y1^(-1/5) for the polytropic term
 // (1/y1)^(21/5) = (1/y1)^4 y1^(-1/5) (Sec. 4.2, exponent 3 gamma = 21/5), and
-// the step-size controller needs E^(-1/5).  The FP64 routine (inv_fifth_root
-// in rhs.cuh) refines a float seed with 7 FP64 instructions; on GB300, whose
-// FP64 pipe retires 2 lanes per clock per SM against the integer pipe's 64,
-// this one does the same refinement in 64-bit fixed point:
+// the step-size controller needs E^(-1/5).  Refining a float seed in FP64
+// costs 7 FP64 instructions; on GB300, whose FP64 pipe retires 2 lanes per
+// clock per SM against the integer pipe's 64, this routine does the
+// refinement in 64-bit fixed point:
 //
 //   1. x = m 2^e with m in [1, 2); e = 5 q + k with k in 0..4, so
 //      x^(-1/5) = u^(-1/5) 2^(-q) with u = m 2^k in [1, 32) and

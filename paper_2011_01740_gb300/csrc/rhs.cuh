@@ -67,45 +67,6 @@ struct Lorenz {
   }
 };
 
-// Exact reinterpretation between a positive double and a float with the same
-// exponent, done on the integer pipe (a double <-> float conversion
-// instruction costs about one FP64 pipe slot on this part).  The exponent is
-// rebiased (1023 -> 127) and the significand truncated to 23 bits, so the
-// float is within 2^-23 relative of x; valid for 2^-126 <= x < 2^128.
-__device__ __forceinline__ float f64_to_f32_trunc(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  return __uint_as_float(((hi - ((1023u - 127u) << 20)) << 3) | (lo >> 29));
-}
-// The inverse, exact for positive normal floats.
-__device__ __forceinline__ double f32_to_f64(float v) {
-  const unsigned b = __float_as_uint(v);
-  return __hiloint2double((int)((b >> 3) + ((1023u - 127u) << 20)), (int)(b << 29));
-}
-
-// x^(-1/5) for 2^-126 <= x < 2^128 (NaN for x <= 0, as pow() gives for the
-// negative bases it is used on).  Float seed from the hardware base-2
-// logarithm and exponential (PTX lg2.approx / ex2.approx, about 22 correct
-// bits, on the integer-reinterpreted float of x), then one third-order step
-// of the binomial series of (1 - r)^(-1/5) with the residual r = 1 - x v^5:
-//   v <- v (1 + r / 5 + 3 r^2 / 25).
-// The neglected r^3 term (11 r^3 / 125) is below 2^-58 for the seed's
-// accuracy, so the result is within about 2 ulp of x^(-1/5).  Cost: 7 FP64
-// instructions, against roughly a hundred for pow().  The FP64 kernels take
-// inv_fifth_root_fx (fifth_root_fx.cuh: the same step in fixed point on the
-// integer pipe); this one serves the double-float kernels' controller, whose
-// FP64 pipe is their spare one.
-__device__ __forceinline__ double inv_fifth_root(double x) {
-  const float xf = f64_to_f32_trunc(x);
-  float l, vf;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(xf));
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(vf) : "f"(-0.2f * l));
-  const double v = f32_to_f64(vf);
-  const double v2 = v * v;
-  const double r = fma(-x, (v2 * v2) * v, 1.0);
-  const double res = fma(v * fma(0.12, r, 0.2), r, v);
-  return __double2hiint(x) > 0 ? res : __longlong_as_double(0x7ff8000000000000LL);
-}
-
 // 1/d to about 1 ulp: the hardware reciprocal approximation (PTX
 // rcp.approx.ftz.f64, on the leading bits of d) refined by one cubic
 // Newton-Raphson step, v (1 + e + e^2) with e = 1 - d v, which cubes the

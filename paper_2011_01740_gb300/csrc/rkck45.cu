@@ -168,7 +168,7 @@ __device__ __forceinline__ bool accept(double E) { return nnbits(E) <= nnbits(1.
 
 // fac = clamp(0.9 E^(-1/5), 0.2, 5).  0.9 E^(-1/5) leaves [0.2, 5] for
 // E > 4.5^5 = 1845.3 and E < 0.18^5 = 1.9e-4, so E is clamped to [1e-4, 2000]
-// first (same result, and keeps inv_fifth_root inside the float range).
+// first (same result, and keeps the float seed of inv_fifth_root_fx in range).
 // E >= 0 or NaN as err_norm returns it.
 __device__ __forceinline__ double step_factor(double E) {
   if (nnbits(E) > nnbits(__longlong_as_double(0x7ff0000000000000LL))) return 0.2;  // NaN
